@@ -1,0 +1,359 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself:
+brute-force loops, closed forms, counting identities, invariants and special
+cases that reduce to a textbook routine.  CPU only."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import apply as OA
+from oracle import fresnel as OF
+from oracle import mpo as OM
+from oracle import mps as OS
+from oracle import quantics as OQ
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b))
+
+
+# ----------------------------------------------------------------------------- quantics map (Sec. III)
+
+@pytest.mark.parametrize("layout", ["serial", "interleaved"])
+def test_quantics_map_matches_bitwise_definition(layout):
+    n = 3
+    L = 1 << n
+    E = np.arange(L * L).reshape(L, L)
+    v = OQ.dense_to_quantics(E, layout)
+    for a in range(L):
+        for b in range(L):
+            assert v[OQ.quantics_index(a, b, n, layout)] == E[a, b]
+    assert np.array_equal(OQ.quantics_to_dense(v, n, layout), E)
+
+
+def test_interleaved_digit_is_two_x_plus_y():
+    # pixel (a, b) = (5, 3) on L = 8: x bits 101, y bits 011 -> mu = (2, 1, 3)
+    n = 3
+    idx = OQ.quantics_index(5, 3, n, "interleaved")
+    assert OQ.site_digits(idx, n, 4) == [2 * 1 + 0, 2 * 0 + 1, 2 * 1 + 1]
+
+
+# ----------------------------------------------------------------------------- TT-SVD (Sec. IV, App. A)
+
+def test_untruncated_tt_svd_is_exact_and_has_page_ranks():
+    rng = np.random.default_rng(1)
+    N = 10
+    v = rng.standard_normal(2 ** N) + 1j * rng.standard_normal(2 ** N)
+    sites, eps = OS.tt_svd(v, N, 2)
+    assert rel(OS.to_vector(sites), v) < 1e-12
+    assert OS.bonds(sites) == [min(2 ** k, 2 ** (N - k)) for k in range(N + 1)]
+    # Sec. IV: a generic binary MPS has D_max = 8/3 * 2^N parameters (exactly 8 (2^N - 1) / 3 for even N)
+    D = sum(A.size for A in sites)
+    assert D == 8 * (2 ** N - 1) // 3
+    assert max(eps) < 1e-20
+
+
+@pytest.mark.parametrize("chi,cutoff", [(6, 0.0), (64, 1e-3), (5, 1e-2)])
+def test_tt_svd_discarded_weights_add_up(chi, cutoff):
+    rng = np.random.default_rng(2)
+    N, d = 6, 4
+    v = rng.standard_normal(d ** N) + 1j * rng.standard_normal(d ** N)
+    v *= np.exp(-0.002 * np.arange(d ** N))
+    sites, eps = OS.tt_svd(v, N, d, chi, cutoff)
+    err2 = np.linalg.norm(OS.to_vector(sites) - v) ** 2
+    assert abs(err2 - sum(eps)) <= 1e-10 * np.linalg.norm(v) ** 2
+    assert max(OS.bonds(sites)) <= chi
+
+
+def test_two_site_truncation_is_eckart_young():
+    # One bond: the canonical truncation is the best rank-k approximation, whose
+    # squared error is the sum of the discarded eigenvalues of M M^dagger.
+    rng = np.random.default_rng(3)
+    M = rng.standard_normal((16, 16)) + 1j * rng.standard_normal((16, 16))
+    sites = [M.reshape(1, 16, 16), np.eye(16, dtype=complex).reshape(16, 16, 1)]
+    k = 5
+    out, eps = OS.truncate(sites, k, 0.0)
+    lam = np.sort(np.linalg.eigvalsh(M @ M.conj().T))[::-1]
+    err2 = np.linalg.norm(OS.to_vector(out) - M.reshape(-1)) ** 2
+    assert abs(err2 - lam[k:].sum()) < 1e-10 * lam.sum()
+    assert abs(eps[0] - lam[k:].sum()) < 1e-10 * lam.sum()
+
+
+def test_canonical_truncation_norm_bookkeeping():
+    sites = synth.random_mps_sites([1, 4, 16, 32, 16, 4, 1], 4, seed=4, decay=0.1)
+    v = OS.to_vector(sites)
+    out, eps = OS.truncate(sites, 8, 0.0)
+    w = OS.to_vector(out)
+    n2 = np.linalg.norm(v) ** 2
+    assert abs(np.linalg.norm(v - w) ** 2 - sum(eps)) < 1e-10 * n2
+    assert abs(np.linalg.norm(w) ** 2 - (n2 - sum(eps))) < 1e-10 * n2
+    assert OS.is_right_canonical(out)
+
+
+def test_keep_rank_rule_brute_force():
+    s = np.array([3.0, 2.0, 1.0, 0.5, 0.1])
+    w = s ** 2
+    for cutoff in [0.0, 1e-4, 0.002, 0.01, 0.05, 0.2, 1.0]:
+        for chi in [1, 2, 3, 10]:
+            k = 1
+            while k < len(s) and w[k:].sum() > cutoff * w.sum():
+                k += 1
+            assert OS.keep_rank(s, chi, cutoff) == min(k, chi)
+
+
+def test_canonical_forms_and_overlaps():
+    sites = synth.random_mps_sites([1, 2, 4, 8, 4, 2, 1], 2, seed=5)
+    v = OS.to_vector(sites)
+    L_ = OS.left_canonicalize(sites)
+    R_ = OS.right_canonicalize(sites)
+    assert OS.is_left_canonical(L_) and OS.is_right_canonical(R_)
+    assert rel(OS.to_vector(L_), v) < 1e-13 and rel(OS.to_vector(R_), v) < 1e-13
+    other = synth.random_mps_sites([1, 2, 3, 3, 3, 2, 1], 2, seed=6)
+    assert abs(OS.overlap(other, sites) - np.vdot(OS.to_vector(other), v)) < 1e-12 * np.linalg.norm(v)
+    digits = [1, 0, 1, 1, 0, 1]
+    flat = int("".join(map(str, digits)), 2)
+    assert abs(OS.amplitude(sites, digits) - v[flat]) < 1e-13
+
+
+def test_elementwise_sum_and_kron():
+    A = synth.random_mps_sites([1, 3, 5, 3, 1], 4, seed=7)
+    B = synth.random_mps_sites([1, 2, 4, 2, 1], 4, seed=8)
+    va, vb = OS.to_vector(A), OS.to_vector(B)
+    assert rel(OS.to_vector(OS.hadamard_product(A, B)), va * vb) < 1e-13
+    assert rel(OS.to_vector(OS.hadamard_product(A, B, conj_b=True)), va * vb.conj()) < 1e-13
+    assert rel(OS.to_vector(OS.direct_sum(A, B)), va + vb) < 1e-13
+    X = synth.random_mps_sites([1, 2, 3, 2, 1], 2, seed=9)
+    Y = synth.random_mps_sites([1, 3, 2, 2, 1], 2, seed=10)
+    E = np.outer(OS.to_vector(X), OS.to_vector(Y))
+    assert rel(OS.to_vector(OS.kron_interleave(X, Y)), OQ.dense_to_quantics(E, "interleaved")) < 1e-13
+
+
+# ----------------------------------------------------------------------------- DFT / QFT (Sec. V)
+
+def test_dft_matrix_brute_force_and_fft_witness():
+    n = 5
+    L = 1 << n
+    rng = np.random.default_rng(11)
+    v = rng.standard_normal(L) + 1j * rng.standard_normal(L)
+    brute = np.array([sum(v[j] * np.exp(2j * np.pi * j * k / L) for j in range(L)) for k in range(L)]) / np.sqrt(L)
+    assert rel(OM.dft_matrix(L) @ v, brute) < 1e-13
+    # library FFT as a third witness: exp(+2 pi i jk/L) is L * ifft
+    assert rel(brute, np.fft.ifft(v) * np.sqrt(L)) < 1e-13
+
+
+def test_qft_circuit_layers_give_bit_reversed_dft():
+    # The uncompressed product of the n circuit layers is the swap-free QFT:
+    # row rev(k) holds DFT row k.
+    n = 5
+    W = OM.identity(n)
+    for j in range(n):
+        W = OM.product(OM.qft_layer(n, j), W)
+    Q = OM.to_dense(W)
+    L = 1 << n
+    for k in range(L):
+        r = OQ.bit_reverse(k, n)
+        for j in range(L):
+            assert abs(Q[r, j] - np.exp(2j * np.pi * j * k / L) / np.sqrt(L)) < 1e-13
+
+
+@pytest.mark.parametrize("n", [4, 6, 8])
+def test_qft_mpo_constructions_agree_and_are_low_rank(n):
+    dense = OM.qft_noswap_dense(n)
+    Wd = OM.qft_mpo_dense(n, 1e-20)
+    Wl = OM.qft_mpo_layers(n, 1e-20)
+    assert np.abs(OM.to_dense(Wd) - dense).max() < 1e-10
+    assert np.abs(OM.to_dense(Wl) - dense).max() < 1e-10
+    # C1 reading: cutoff 1e-10 keeps bond <= 8
+    assert max(OM.bonds(OM.qft_mpo_layers(n, 1e-10))) <= 8
+    Q = OM.to_dense(Wl)
+    assert np.abs(Q.conj().T @ Q - np.eye(1 << n)).max() < 1e-10
+
+
+def test_qft_rank_stays_bounded_with_n():
+    # Sec. V: the QFT has a finite-rank MPO; the bond does not grow with n.
+    ranks = [max(OM.bonds(OM.qft_mpo_layers(n, 1e-12))) for n in (8, 10, 12, 14)]
+    assert max(ranks) <= 8 and len(set(ranks)) == 1
+
+
+def fwht(v):
+    """Fast Walsh-Hadamard transform, orthonormal (own butterfly code)."""
+    v = np.array(v, dtype=np.complex128)
+    h = 1
+    while h < len(v):
+        for i in range(0, len(v), 2 * h):
+            a = v[i:i + h].copy()
+            b = v[i + h:i + 2 * h].copy()
+            v[i:i + h] = a + b
+            v[i + h:i + 2 * h] = a - b
+        h *= 2
+    return v / np.sqrt(len(v))
+
+
+def test_hadamard_mpo_is_rank_one_walsh_transform():
+    n = 6
+    sites = synth.random_mps_sites([1, 2, 4, 8, 4, 2, 1], 2, seed=12)
+    sites = OS.right_canonicalize(sites)
+    H = OM.hadamard_mpo(n)
+    out, eps = OA.zipup(H, sites, 1 << 20, 0.0, "lr")
+    assert rel(OS.to_vector(out), fwht(OS.to_vector(sites))) < 1e-12
+    assert OM.bonds(H) == [1] * (n + 1)
+
+
+def test_phase_mpo_matches_transfer_function():
+    n, c = 8, 0.37
+    W = OM.phase_mpo(n, c, 1e-20)
+    Dm = OM.to_dense(W)
+    L = 1 << n
+    for idx in range(L):
+        k = OQ.bit_reverse(idx, n)
+        kf = k if k < L // 2 else k - L
+        assert abs(Dm[idx, idx] - np.exp(-1j * np.pi * c * kf * kf / L)) < 1e-10
+    assert np.abs(Dm - np.diag(np.diag(Dm))).max() < 1e-10
+    assert max(OM.bonds(OM.phase_mpo(n, 0.0, 1e-14))) == 1
+
+
+# ----------------------------------------------------------------------------- zip-up (Sec. V, Fig. fig_mpo)
+
+@pytest.mark.parametrize("direction", ["lr", "rl"])
+def test_untruncated_zipup_equals_exact_product(direction):
+    n = 6
+    sites = synth.random_mps_sites([1, 2, 4, 8, 4, 2, 1], 2, seed=13)
+    sites = OS.right_canonicalize(sites) if direction == "lr" else OS.left_canonicalize(sites)
+    W = OM.qft_mpo_layers(n, 1e-20)
+    out, eps = OA.zipup(W, sites, 1 << 20, 0.0, direction)
+    assert rel(OS.to_vector(out), OM.to_dense(W) @ OS.to_vector(sites)) < 1e-12
+    check = OS.is_left_canonical if direction == "lr" else OS.is_right_canonical
+    assert check(out)
+
+
+def test_zipup_with_unitary_product_operator_is_sequential_svd():
+    # With a bond-1 MPO of unitaries the right environment of every cut is an
+    # isometry, so each zip-up truncation is the exact SVD of the current
+    # unfolding: the result is TT-SVD of the exactly applied state.
+    n = 6
+    sites = OS.right_canonicalize(synth.random_mps_sites([1, 4, 16, 64, 16, 4, 1], 4, seed=14, decay=0.05))
+    U = synth.random_unitary_sites(n, seed=15, dim=4)
+    W = [u.reshape(1, 4, 4, 1) for u in U]
+    out, eps = OA.zipup(W, sites, 10, 0.0, "lr")
+    ref, eps_ref = OS.tt_svd(OM.to_dense(W) @ OS.to_vector(sites), n, 4, 10, 0.0)
+    assert rel(OS.to_vector(out), OS.to_vector(ref)) < 1e-10
+    assert np.allclose(eps, eps_ref, rtol=1e-9, atol=1e-14)
+
+
+# ----------------------------------------------------------------------------- Fresnel (Sec. VI.A)
+
+def test_dense_fresnel_matches_fft_and_is_unitary():
+    E = synth.gaussian_beam_with_rectangles(5, seed=16, waist=0.2).astype(complex)
+    a, b = OF.fresnel_dense(E, 0.3), OF.fresnel_fft(E, 0.3)
+    assert rel(a, b) < 1e-13
+    assert abs(np.linalg.norm(a) - np.linalg.norm(E)) < 1e-12 * np.linalg.norm(E)
+
+
+@pytest.mark.parametrize("layout", ["interleaved", "serial"])
+def test_untruncated_mps_fresnel_equals_dense(layout):
+    n, c = 5, 0.3
+    E = synth.gaussian_beam_with_rectangles(n, seed=17, waist=0.2).astype(complex)
+    sites, _ = OS.tt_svd(OQ.dense_to_quantics(E, layout), OQ.n_sites(n, layout), OQ.phys_dim(layout))
+    ops = OF.step_operators(n, c, qft=OM.qft_mpo_layers(n, 1e-20), phase_cutoff=1e-20)
+    out, canon, disc = OF.fresnel_mps(sites, layout, n, c, 1 << 20, 0.0, canon="left", ops=ops)
+    Ez = OQ.quantics_to_dense(OS.to_vector(out), n, layout)
+    assert rel(Ez, OF.fresnel_dense(E, c)) < 1e-11
+    assert abs(np.linalg.norm(Ez) - np.linalg.norm(E)) < 1e-11 * np.linalg.norm(E)
+
+
+def test_fresnel_group_properties():
+    n = 4
+    E = synth.gaussian_beam_with_rectangles(n, seed=18, waist=0.3).astype(complex)
+    sites, _ = OS.tt_svd(OQ.dense_to_quantics(E, "interleaved"), n, 4)
+    Q = OM.qft_mpo_layers(n, 1e-20)
+
+    def step(s, c, canon="left"):
+        ops = (Q, OM.dagger(Q), OM.phase_mpo(n, c, 1e-20))
+        return OF.fresnel_mps(s, "interleaved", n, c, 1 << 20, 0.0, canon=canon, ops=ops)
+
+    v0 = OS.to_vector(sites)
+    a, ca, _ = step(sites, 0.0)
+    assert rel(OS.to_vector(a), v0) < 1e-11                      # c = 0 is the identity
+    b, cb, _ = step(*step(sites, 0.4)[:1], -0.4, canon="right")
+    assert rel(OS.to_vector(b), v0) < 1e-11                      # forward then backward
+    two = step(step(sites, 0.25)[0], 0.25, canon="right")[0]
+    one = step(sites, 0.5)[0]
+    assert rel(OS.to_vector(two), OS.to_vector(one)) < 1e-11     # z1 + z2 composes
+
+
+def test_x_and_y_passes_commute():
+    n = 4
+    E = synth.gaussian_beam_with_rectangles(n, seed=19, waist=0.3).astype(complex)
+    v = OQ.dense_to_quantics(E, "interleaved")
+    Q = OM.qft_mpo_layers(n, 1e-20)
+    Wx, Wy = OM.embed(Q, "interleaved", 0, n), OM.embed(Q, "interleaved", 1, n)
+    Dx, Dy = OM.to_dense(Wx), OM.to_dense(Wy)
+    assert np.abs(Dx @ Dy - Dy @ Dx).max() < 1e-12
+    # acting on x alone is the 1-D transform of every column
+    Qd = OM.to_dense(Q)
+    assert rel(OQ.quantics_to_dense(Dx @ v, n, "interleaved"), Qd @ E) < 1e-12
+
+
+def test_fourier_space_phase_identity():
+    # Q psi_out = D (Q psi_in): the step is diagonal in (bit-reversed) Fourier space.
+    n, c = 5, 0.7
+    L = 1 << n
+    rng = np.random.default_rng(20)
+    v = rng.standard_normal(L) + 1j * rng.standard_normal(L)
+    out = OF.fresnel_dense_1d(v, c)
+    Q = OM.qft_noswap_dense(n)
+    D = OM.phase_vector(n, c, True)
+    assert rel(Q @ out, D * (Q @ v)) < 1e-12
+
+
+def test_hilbert_transform_pipeline():
+    # Sec. VI.C: Q^dagger (-i Z_n) Q with a bond-1 diagonal is the periodic
+    # Hilbert-type transform: multiply frequency k by -i for k < L/2, +i otherwise.
+    n = 6
+    L = 1 << n
+    sites = OS.right_canonicalize(synth.random_mps_sites([1, 2, 4, 8, 4, 2, 1], 2, seed=21))
+    v = OS.to_vector(sites)
+    Q = OM.qft_mpo_layers(n, 1e-20)
+    A, canon, _ = OF.apply_sequence([Q, OM.hilbert_diag_mpo(n), OM.dagger(Q)], sites, "right", 1 << 20, 0.0)
+    F = OM.dft_matrix(L)
+    sgn = np.where(np.arange(L) < L // 2, -1j, 1j)
+    assert rel(OS.to_vector(A), F.conj().T @ (sgn * (F @ v))) < 1e-11
+
+
+def test_gaussian_beam_closed_form_1d():
+    # Textbook Fresnel propagation of a Gaussian (not in the paper); the grid
+    # is fine enough and wide enough that sampling and wrap-around are < 1e-10.
+    n = 10
+    L = 1 << n
+    x = np.arange(L) - L / 2
+    w = 0.06 * L
+    lz = 0.8 * L                                 # lambda z / dx^2 in pixel units
+    c = lz / L
+    v = np.exp(-x * x / (w * w))
+    sites, _ = OS.tt_svd(np.roll(v, 0), n, 2, 1 << 20, 1e-24)
+    out, canon, _ = OF.fresnel_mps(sites, "1d", n, c, 1 << 20, 1e-24, canon="left",
+                                   ops=OF.step_operators(n, c, qft=OM.qft_mpo_layers(n, 1e-22), phase_cutoff=1e-24))
+    got = OS.to_vector(out)
+    ref = OF.gaussian_closed_form(x, w, lz)
+    assert np.abs(got - ref).max() < 1e-9
+
+
+def test_c1_image_qft_against_brute_force_dft():
+    # C1: 64x64 image, serial 12 sites, TT-SVD chi 16, QFT MPO cutoff 1e-10.
+    # Q is unitary, so ||Q psi~ - Q psi|| = ||psi~ - psi|| = sqrt(sum eps).
+    n = 6
+    L = 1 << n
+    img = synth.gaussian_random_field_image(n)
+    v = OQ.dense_to_quantics(img, "serial")
+    sites, eps = OS.tt_svd(v, 2 * n, 2, 16, 0.0)
+    Q = OM.qft_mpo_layers(n, 1e-10)
+    out, canon, _ = OF.apply_sequence([OM.embed(Q, "serial", 0, n), OM.embed(Q, "serial", 1, n)],
+                                      sites, "left", 1 << 20, 0.0)
+    F = OM.dft_matrix(L)
+    ref = F @ img @ F.T
+    perm = [OQ.bit_reverse(k, n) for k in range(L)]
+    ref_br = np.empty_like(ref)
+    ref_br[np.ix_(perm, perm)] = ref
+    got = OQ.quantics_to_dense(OS.to_vector(out), n, "serial")
+    err = np.linalg.norm(got - ref_br)
+    assert err <= np.sqrt(sum(eps)) + 1e-6 * np.linalg.norm(img)
+    assert max(OS.bonds(sites)) <= 16
