@@ -1,0 +1,207 @@
+/*
+ * qtn.h -- C ABI of the quantics tensor-network Fresnel library (CUDA, sm_103a).
+ *
+ * The library implements the hot path of arXiv:2510.23089 ("Tensor network
+ * methods for quantum-inspired image processing and classical optics"):
+ * a 2^n x 2^n field is encoded as a quantics MPS by sequential truncated SVD
+ * (Sec. III, Sec. IV, App. A) and propagated by the Fresnel transfer function
+ * in that compressed form as U_QFT^dagger U(z) U_QFT (Sec. VI.A, Fig.
+ * fig_mpo_mpo), each operator applied per axis as an MPO by zip-up
+ * contraction with SVD truncation (Sec. V, Fig. fig_mpo).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Plain C types only; every pointer documented "device" must be CUDA device
+ *    memory owned by the caller.  The library never allocates or frees device
+ *    memory: scratch space is the caller's workspace (see qtn_workspace_size).
+ *  - All work is enqueued on the stream given to qtn_create and is
+ *    stream-ordered.  No entry point synchronises the stream except when a
+ *    non-NULL qtn_stats* is passed, in which case the call waits for its own
+ *    work and copies the statistics to that host struct.
+ *  - Complex numbers are interleaved single precision (re, im) pairs
+ *    ("complex64", 8 bytes), C99 float _Complex / CUDA float2 layout.
+ *  - Bond dimensions chosen by truncation live in device int arrays so that a
+ *    whole sequence of calls can be captured in a CUDA graph; kernels are sized
+ *    by capacities.
+ *  - Errors are returned as qtn_status; nothing is truncated silently: a bond
+ *    that would exceed its capacity is clamped to the capacity and the call
+ *    reports QTN_ERR_CAPACITY through the statistics flags.
+ */
+#ifndef QTN_H
+#define QTN_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QTN_OK = 0,
+    QTN_ERR_ARG = 1,        /* invalid argument (NULL pointer, bad enum, bad size) */
+    QTN_ERR_SHAPE = 2,      /* inconsistent shapes between arguments */
+    QTN_ERR_CAPACITY = 3,   /* a result does not fit the caller's capacity */
+    QTN_ERR_NOCONV = 4,     /* an iterative eigen/SVD solve hit max_sweeps unconverged */
+    QTN_ERR_NONFINITE = 5,  /* NaN or Inf met in the input or produced */
+    QTN_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up */
+    QTN_ERR_CUDA = 7,       /* a CUDA runtime call failed */
+    QTN_ERR_BOUNDS = 8,     /* an index was out of range (checked builds) */
+    QTN_ERR_WORKSPACE = 9   /* the workspace is NULL or smaller than required */
+} qtn_status;
+
+/* Quantics index layouts (Sec. III).  Bits are most-significant first:
+ * a = sum_p x_p 2^(n-p).
+ *   SERIAL      2n sites of d = 2, (x_1..x_n, y_1..y_n): row-major flattening.
+ *   INTERLEAVED n sites of d = 4, site p holds mu_p = (x_p y_p)_2 = 2 x_p + y_p.
+ *   ONE_D       n sites of d = 2 for a single axis (a vector of 2^n samples). */
+typedef enum { QTN_LAYOUT_SERIAL = 0, QTN_LAYOUT_INTERLEAVED = 1, QTN_LAYOUT_1D = 2 } qtn_layout;
+
+/* Arithmetic of the site contractions.  PLAIN_FP32: FP32 SIMT FMA.
+ * MIXED: BF16 tensor-core products with FP32 accumulation (tcgen05). */
+typedef enum { QTN_PLAIN_FP32 = 0, QTN_MIXED = 1 } qtn_precision;
+
+/* Canonical form of an MPS, tracked on the host by the library. */
+typedef enum { QTN_CANON_NONE = 0, QTN_CANON_LEFT = 1, QTN_CANON_RIGHT = 2 } qtn_canon;
+
+/* Matrix product state (Sec. IV, MPS factorisation):
+ *   psi[s_1..s_N] = A_1[:, s_1, :] ... A_N[:, s_N, :].
+ * Site p (0-based) is stored padded at
+ *   sites + p * chi_cap*d*chi_cap, element (l, s, r) at (l*d + s)*chi_cap + r,
+ * with l < bond[p], r < bond[p+1]; bond[0] = bond[N] = 1.
+ * LEFT canonical: sites 0..N-2 are left isometries, the norm sits in site N-1.
+ * RIGHT canonical: sites 1..N-1 are right isometries, the norm sits in site 0. */
+typedef struct {
+    int n_sites;     /* N >= 1 */
+    int d;           /* physical dimension, 2 or 4 */
+    int chi_cap;     /* capacity of every bond */
+    int canon;       /* qtn_canon; updated by the library */
+    int* bond;       /* device int[N+1] */
+    void* sites;     /* device complex64 [N][chi_cap][d][chi_cap] */
+} qtn_mps;
+
+/* Per-axis matrix product operator on n sites of d = 2 (Sec. V, Fig. fig_mpo):
+ *   O[s'_1..s'_n, s_1..s_n] = W_1[:, s'_1, s_1, :] ... W_n[:, s'_n, s_n, :].
+ * Core p stored padded at sites + p * w_cap*4*w_cap, element (a, s', s, b) at
+ * ((a*2 + s')*2 + s)*w_cap + b.  w_max is the largest bond (host copy). */
+typedef struct {
+    int n_sites;
+    int w_cap;
+    int w_max;       /* host-side max over bond[]; set by the builders */
+    int* bond;       /* device int[n+1] */
+    void* sites;     /* device complex64 [n][w_cap][2][2][w_cap] */
+} qtn_mpo;
+
+/* Truncation rule: keep the smallest k >= 1 whose discarded weight
+ * sum_{i>=k} s_i^2 is at most cutoff * sum_i s_i^2, capped by chi_max
+ * (the paper's relative cutoff, Sec. VI.B.3, read as a relative weight). */
+typedef struct {
+    int chi_max;
+    double cutoff;
+    int prec;         /* qtn_precision */
+    int max_sweeps;   /* Jacobi sweep limit per eigen-solve (0 = default 30) */
+} qtn_trunc;
+
+/* Statistics of one call (filled only when a non-NULL pointer is passed). */
+typedef struct {
+    double discarded;   /* sum of discarded squared singular values (FP64) */
+    double norm2;       /* squared norm of the result (FP64) */
+    int max_bond;       /* largest bond of the result */
+    int sweeps_used;    /* largest Jacobi sweep count of any solve */
+    int flags;          /* bit 0: some solve did not converge; bit 1: a bond was clamped to capacity;
+                           bit 2: non-finite value met */
+} qtn_stats;
+
+/* Library context bound to one CUDA stream (cudaStream_t passed as void*;
+ * NULL = legacy default stream).  Owns no device memory. */
+qtn_status qtn_create(void** ctx, void* cuda_stream);
+qtn_status qtn_destroy(void* ctx);
+qtn_status qtn_set_stream(void* ctx, void* cuda_stream);
+const char* qtn_status_string(qtn_status s);
+int qtn_version(void);
+
+/* Bytes of device workspace needed by any call on states of n_sites sites of
+ * dimension d with bonds up to chi_max, MPOs with bonds up to w_max, and
+ * (for qtn_encode) dense inputs of dense_elems complex entries. */
+qtn_status qtn_workspace_size(void* ctx, int n_sites, int d, int chi_max, int w_max,
+                              long long dense_elems, size_t* bytes);
+
+/* TT-SVD encoding (Sec. IV, Fig. MPS; App. A): sequential truncated SVD of the
+ * quantics tensor of a dense field, left to right.
+ *   dense      device complex64; layout SERIAL/INTERLEAVED: L x L row-major
+ *              (row = x, column = y), L = 2^n; layout 1D: 2^n entries.
+ *   out        caller-allocated MPS with n_sites/d matching the layout and
+ *              chi_cap >= trunc.chi_max; overwritten; result LEFT canonical.
+ *   stats      optional; discarded = sum of per-bond discarded weights. */
+qtn_status qtn_encode(void* ctx, const void* dense, int n, qtn_layout layout, qtn_trunc trunc,
+                      qtn_mps* out, qtn_stats* stats, void* ws, size_t ws_bytes);
+
+/* Swap-free quantum Fourier transform MPO (Sec. V: the QFT as a finite-rank MPO):
+ * unitary kernel exp(+2 pi i j k / L)/sqrt(L), output site p carries frequency
+ * bit k_{n+1-p} (bit-reversed order).  Built on the device as the product of
+ * the n circuit layers (H, then controlled phases), compressed after every
+ * layer with relative cutoff `cutoff`.  inverse != 0 gives the Hermitian
+ * conjugate.  out->w_cap must be >= 16. */
+qtn_status qtn_build_qft_mpo(void* ctx, int n, int inverse, double cutoff, qtn_mpo* out,
+                             void* ws, size_t ws_bytes);
+
+/* Quadratic-phase (Fresnel transfer function) diagonal MPO (Sec. VI.A:
+ * T_z(f) = exp(-i pi lambda z f^2)): diagonal entry of frequency k is
+ * exp(-i pi c k_f^2 / L) with k_f the signed fftfreq integer and
+ * c = lambda z / (L dx^2); indexed in bit-reversed order when bit_reversed != 0
+ * (matching the swap-free QFT output).  Built by TT-SVD of the 2^n diagonal. */
+qtn_status qtn_build_phase_mpo(void* ctx, int n, double c, int bit_reversed, double cutoff,
+                               qtn_mpo* out, void* ws, size_t ws_bytes);
+
+/* Hermitian conjugate of an MPO: out[a, s', s, b] = conj(in[a, s, s', b]). */
+qtn_status qtn_mpo_dagger(void* ctx, const qtn_mpo* in, qtn_mpo* out);
+
+/* Zip-up MPO x MPS application with SVD truncation (Sec. V, Fig. fig_mpo).
+ * The per-axis MPO W acts on axis `axis` (0 = x, 1 = y) of psi:
+ *   INTERLEAVED: on the x (high) or y (low) bit of every d = 4 site;
+ *   SERIAL: on sites [axis*n, axis*n + n); 1D: on all sites (axis ignored).
+ * Direction follows psi->canon: LEFT -> right-to-left sweep (result RIGHT
+ * canonical), RIGHT -> left-to-right (result LEFT); NONE is first brought to
+ * LEFT canonical form without truncation.  psi is updated in place. */
+qtn_status qtn_apply_mpo(void* ctx, const qtn_mpo* W, int axis, qtn_mps* psi, qtn_trunc trunc,
+                         qtn_stats* stats, void* ws, size_t ws_bytes);
+
+/* Canonical SVD compression (Sec. IV; every truncation acts on a Schmidt
+ * decomposition, App. A): left sweep without truncation, then right-to-left
+ * truncating sweep.  Result RIGHT canonical; stats.discarded is the exact
+ * squared error (Eckart-Young per bond). */
+qtn_status qtn_truncate(void* ctx, qtn_mps* psi, qtn_trunc trunc, qtn_stats* stats,
+                        void* ws, size_t ws_bytes);
+
+/* n_steps Fresnel steps (Fig. fig_mpo_mpo): per step Q_x, Q_y, D_x, D_y,
+ * Qd_x, Qd_y applied in this order by qtn_apply_mpo (alternating sweep
+ * directions).  Q = qft, Qd = its dagger, D = phase (all per-axis MPOs on the
+ * state's n = bits per axis).  For layout 1D only the x passes run. */
+qtn_status qtn_fresnel_step(void* ctx, qtn_mps* psi, qtn_layout layout, const qtn_mpo* qft,
+                            const qtn_mpo* qft_dagger, const qtn_mpo* phase, int n_steps,
+                            qtn_trunc trunc, qtn_stats* stats, void* ws, size_t ws_bytes);
+
+/* Contract an MPS to its dense field (inverse quantics map of the layout).
+ * dense: device complex64 with room for cap_elems entries; the field has
+ * d^N entries, written L x L row-major for SERIAL/INTERLEAVED.
+ * QTN_ERR_CAPACITY if d^N > cap_elems. */
+qtn_status qtn_to_dense(void* ctx, const qtn_mps* psi, qtn_layout layout, void* dense,
+                        long long cap_elems, void* ws, size_t ws_bytes);
+
+/* Squared norm <psi|psi> in FP64 (transfer matrices; never densifies).
+ * norm2: host double, written after the call's stream work completes. */
+qtn_status qtn_norm2(void* ctx, const qtn_mps* psi, double* norm2, void* ws, size_t ws_bytes);
+
+/* Overlap <a|b> (complex, FP64 accumulation) by transfer matrices.
+ * result: host double[2] (re, im); the call synchronises. */
+qtn_status qtn_overlap(void* ctx, const qtn_mps* a, const qtn_mps* b, double* result,
+                       void* ws, size_t ws_bytes);
+
+/* Amplitudes psi[s] for `count` site-digit strings (O(N chi^2) each).
+ * digits: device int[count][N]; out: device complex64[count]. */
+qtn_status qtn_amplitudes(void* ctx, const qtn_mps* psi, const int* digits, int count, void* out,
+                          void* ws, size_t ws_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QTN_H */

@@ -1,0 +1,473 @@
+// Site-level kernels of the zip-up sweep, encoder, MPO builders and contractions.
+//
+// Sweep orientation: a right-to-left pass is a left-to-right pass over the
+// mirrored chain (sites reversed, left/right bonds swapped).  Kernels take a
+// `mirror` flag and read/write the physical padded layout accordingly, so no
+// site is ever copied to change orientation.
+#include <math.h>
+
+#include "qtn_internal.cuh"
+
+namespace qtn {
+
+// ------------------------------------------------------------------ planning
+
+// Dimensions of zip-up site p (sweep order) -> dimension registers.
+__global__ void k_plan_site(const int* __restrict__ bond, const int* __restrict__ mbond, int N, int d, int mirror,
+                           int moff, int mn, int p, int* __restrict__ R) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int q = mirror ? N - 1 - p : p;
+    const int chiL = (p == 0) ? 1 : R[R_CHIR];
+    const int chiLn = (p == 0) ? 1 : R[R_K];
+    const int wl = (p == 0) ? 1 : R[R_WR];
+    const int chiR = mirror ? bond[q] : bond[q + 1];
+    const int qm = q - moff;
+    int wr = 1;
+    if (mbond != nullptr && qm >= 0 && qm < mn) wr = mirror ? mbond[qm] : mbond[qm + 1];
+    R[R_CHILN] = chiLn;
+    R[R_CHIL] = chiL;
+    R[R_CHIR] = chiR;
+    R[R_WL] = wl;
+    R[R_WR] = wr;
+    R[R_M] = chiLn * d;
+    R[R_N] = wr * chiR;
+    R[R_MID] = chiLn * wl;
+    R[R_DN] = d * chiR;
+    R[R_LAST] = (p == N - 1);
+    R[R_P] = min(chiLn * d, EIG_MAX);
+}
+
+// Encoder bond p: rows = previous rank * d, columns fixed by the host.
+__global__ void k_plan_encode(int p, int d, int* __restrict__ R) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int r = (p == 0) ? 1 : R[R_K];
+    R[R_CHILN] = r;
+    R[R_M] = r * d;
+    R[R_P] = min(r * d, EIG_MAX);
+}
+
+__global__ void k_reset_stats(int* __restrict__ R, double* __restrict__ ledger) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        R[R_SWEEPS] = 0;
+        R[R_FLAGS] = 0;
+        R[R_MAXBOND] = 0;
+        R[R_K] = 1;
+        R[R_CHIR] = 1;
+        R[R_WR] = 1;
+        for (int i = 0; i < L_COUNT; ++i) ledger[i] = 0.0;
+    }
+}
+
+// ------------------------------------------------------------------ contraction, second stage
+// T[(x, t'), (b, k)] = sum_{a, t} P[(x, a), (t, k)] W[a, t', t, b] with the MPO acting on one bit of the
+// physical index (d = 4: bit `axis` selects x = high or y = low; the other bit passes through).
+__global__ void k_stage2(const float2* __restrict__ P, float2* __restrict__ T, const float2* __restrict__ Wc,
+                         int wcap, int mirror, int d, int axis, const int* __restrict__ R) {
+    const int chiLn = R[R_CHILN], wl = R[R_WL], wr = R[R_WR], chiR = R[R_CHIR];
+    const int m = chiLn * d, n = wr * chiR;
+    const long long total = (long long)m * n;
+    const int dn = d * chiR;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int row = (int)(e / n), col = (int)(e % n);
+        const int x = row / d, sp = row % d;
+        const int b = col / chiR, k = col % chiR;
+        if (Wc == nullptr) {
+            T[e] = P[(long long)x * dn + sp * chiR + k];
+            continue;
+        }
+        int t, so;
+        if (d == 2) { t = sp; so = 0; }
+        else if (axis == 0) { t = sp >> 1; so = sp & 1; }
+        else { t = sp & 1; so = sp >> 1; }
+        float2 acc = make_float2(0.f, 0.f);
+        for (int a = 0; a < wl; ++a) {
+            const float2* prow = P + (long long)(x * wl + a) * dn;
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const int sf = (d == 2) ? s : (axis == 0 ? ((s << 1) | so) : ((so << 1) | s));
+                const float2 w = mirror ? Wc[((b * 2 + t) * 2 + s) * wcap + a] : Wc[((a * 2 + t) * 2 + s) * wcap + b];
+                cfma(acc, prow[sf * chiR + k], w);
+            }
+        }
+        T[e] = acc;
+    }
+}
+
+// ------------------------------------------------------------------ truncation bookkeeping
+
+// Trace of an FP64 Gram matrix (total weight of the factorised matrix) -> ledger[L_TRACE].
+__global__ void k_trace(const double2* __restrict__ G, int ld, Dim rdim, const int* __restrict__ R,
+                        double* __restrict__ ledger) {
+    const int r = rdim.eval(R);
+    double s = 0.0;
+    for (int i = threadIdx.x; i < r; i += blockDim.x) s += G[(long long)i * ld + i].x;
+    __shared__ double red[32];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += red[w];
+        ledger[L_TRACE] = t;
+    }
+}
+
+// Squared norms of the rows of X (FP64 accumulation): w[i] = sum_c |X[i, c]|^2.
+__global__ void k_row_weights(const float2* __restrict__ X, Dim ldx, Dim rows, Dim cols, double* __restrict__ w,
+                              const int* __restrict__ R) {
+    const int r = rows.eval(R), n = cols.eval(R);
+    const long long ld = ldx.eval(R);
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < r; i += nwarps) {
+        double s = 0.0;
+        const float2* row = X + (long long)i * ld;
+        for (int c = lane; c < n; c += 32) {
+            float2 v = row[c];
+            s += (double)v.x * v.x + (double)v.y * v.y;
+        }
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) w[i] = s;
+    }
+}
+
+// Truncation rule on projected weights: sort descending, keep the smallest k >= 1 whose discarded
+// weight (total - kept) is <= cutoff * total, cap by chi_max and the capacity.  total = trace of the
+// Gram matrix (the exact weight of the factorised matrix).  Writes perm[0..k), R[R_K], discarded.
+__global__ void k_select(const double* __restrict__ w, Dim rdim, int chi_max, double cutoff, int chi_cap,
+                         int* __restrict__ perm, int* __restrict__ R, double* __restrict__ ledger) {
+    __shared__ double sorted_w[1024];
+    const int r = rdim.eval(R);
+    for (int j = threadIdx.x; j < r; j += blockDim.x) {
+        const double v = w[j];
+        int rk = 0;
+        for (int i = 0; i < r; ++i) {
+            const double u = w[i];
+            rk += (u > v) || (u == v && i < j);
+        }
+        sorted_w[rk] = v;
+        perm[rk] = j;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double total = ledger[L_TRACE];
+        double kept = 0.0;
+        int k = 0;
+        // directions whose captured weight is below NULL_FLOOR * total are numerically null for FP32 data
+        // (singular value below ~1e-7 of the norm): they are never kept, whatever the cutoff.
+        const double NULL_FLOOR = 1e-14;
+        while (k < r) {
+            if (k >= 1 && total - kept <= cutoff * total) break;
+            if (k >= 1 && !(sorted_w[k] > NULL_FLOOR * total)) break;
+            kept += sorted_w[k];
+            ++k;
+        }
+        if (k < 1) k = 1;
+        int kk = min(k, chi_max);
+        if (kk > chi_cap) { kk = chi_cap; R[R_FLAGS] |= 2; }
+        kept = 0.0;
+        for (int i = 0; i < kk; ++i) kept += sorted_w[i];
+        double disc = total - kept;
+        if (disc < 0.0) disc = 0.0;
+        ledger[L_DISCARDED] += disc;
+        if (!(total == total)) R[R_FLAGS] |= 4;
+        R[R_K] = kk;
+        R[R_MAXBOND] = max(R[R_MAXBOND], kk);
+    }
+}
+
+// New site from kept left singular vectors: site[(x, t), j] = U[perm[j]][(x, t)] (U column-major), written
+// in the physical layout of the sweep orientation; also stores the new bond.
+__global__ void k_write_site(const float2* __restrict__ U, int ldu, const int* __restrict__ perm,
+                             float2* __restrict__ site, int cap, int d, int mirror, int* __restrict__ bond,
+                             int bond_index, const int* __restrict__ R) {
+    const int chiLn = R[R_CHILN], k = R[R_K];
+    const int total = chiLn * d * k;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int x = e / (d * k), t = (e / k) % d, j = e % k;
+        const float2 v = U[(long long)perm[j] * ldu + x * d + t];
+        if (mirror) site[((long long)j * d + t) * cap + x] = v;
+        else site[((long long)x * d + t) * cap + j] = v;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) bond[bond_index] = k;
+}
+
+// Carry rows in kept order: C[j, :] = X[perm[j], :].
+__global__ void k_gather_rows(const float2* __restrict__ X, Dim ldx, const int* __restrict__ perm,
+                              float2* __restrict__ C, Dim ldc, Dim cols, const int* __restrict__ R) {
+    const int k = R[R_K], n = cols.eval(R);
+    const long long lx = ldx.eval(R), lc = ldc.eval(R);
+    const long long total = (long long)k * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(e / n), c = (int)(e % n);
+        C[(long long)j * lc + c] = X[(long long)perm[j] * lx + c];
+    }
+}
+
+// Last site of a sweep: the whole (x, t) column of T (n = 1) becomes the site.
+__global__ void k_write_last(const float2* __restrict__ T, float2* __restrict__ site, int cap, int d, int mirror,
+                             const int* __restrict__ R) {
+    const int chiLn = R[R_CHILN];
+    for (int e = threadIdx.x; e < chiLn * d; e += blockDim.x) {
+        const int x = e / d, t = e % d;
+        if (mirror) site[(long long)t * cap + x] = T[e];
+        else site[((long long)x * d + t) * cap] = T[e];
+    }
+}
+
+// Squared Frobenius norm of a padded site (l < bl, r < br) -> ledger[slot] (FP64).
+__global__ void k_site_norm2(const float2* __restrict__ site, int cap, int d, const int* __restrict__ bond, int q,
+                             double* __restrict__ ledger, int slot) {
+    const int bl = bond[q], br = bond[q + 1];
+    const int total = bl * d * br;
+    double s = 0.0;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int l = e / (d * br), t = (e / br) % d, r = e % br;
+        const float2 v = site[((long long)l * d + t) * cap + r];
+        s += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    __shared__ double red[32];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += red[w];
+        ledger[slot] = t;
+    }
+}
+
+// Convert an FP64 matrix to FP32 (r x r, same leading dimension).
+__global__ void k_to_f32(const double2* __restrict__ G, float2* __restrict__ G32, int ld, Dim rdim,
+                         const int* __restrict__ R) {
+    const int r = rdim.eval(R);
+    const long long total = (long long)r * r;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / r), j = (int)(e % r);
+        const double2 g = G[(long long)i * ld + j];
+        G32[(long long)i * ld + j] = make_float2((float)g.x, (float)g.y);
+    }
+}
+
+// Whitening of an eigenbasis: Z[:, j] /= sqrt(lam_j), zeroed below floor * lam_0 (lam sorted descending).
+__global__ void k_whiten(float2* __restrict__ Z, int ldz, const double* __restrict__ lam, Dim rdim, double floor_rel,
+                         const int* __restrict__ R) {
+    const int r = rdim.eval(R);
+    const double l0 = lam[0];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * r; e += gridDim.x * blockDim.x) {
+        const int j = e / r, i = e % r;
+        const double l = lam[j];
+        const float s = (l > floor_rel * l0 && l > 0.0) ? (float)(1.0 / sqrt(l)) : 0.f;
+        float2* z = Z + (long long)j * ldz + i;
+        *z = cscale(*z, s);
+    }
+}
+
+// ------------------------------------------------------------------ quantics permutations
+
+__device__ __forceinline__ unsigned compact_bits(unsigned long long v, int n) {
+    // gather bits 0, 2, 4, ... of v (n of them) into an integer
+    unsigned out = 0;
+    for (int i = 0; i < n; ++i) out |= (unsigned)((v >> (2 * i)) & 1ull) << i;
+    return out;
+}
+
+// dense (row-major L x L, or 2^n vector for 1D) -> quantics-ordered vector
+__global__ void k_dense_to_quantics(const float2* __restrict__ dense, float2* __restrict__ out, int n, int layout) {
+    const long long total = (layout == QTN_LAYOUT_1D) ? (1ll << n) : (1ll << (2 * n));
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        if (layout == QTN_LAYOUT_INTERLEAVED) {
+            const unsigned a = compact_bits((unsigned long long)idx >> 1, n);
+            const unsigned b = compact_bits((unsigned long long)idx, n);
+            out[idx] = dense[((long long)a << n) | b];
+        } else {
+            out[idx] = dense[idx];
+        }
+    }
+}
+
+__global__ void k_quantics_to_dense(const float2* __restrict__ q, float2* __restrict__ dense, int n, int layout) {
+    const long long total = (layout == QTN_LAYOUT_1D) ? (1ll << n) : (1ll << (2 * n));
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        if (layout == QTN_LAYOUT_INTERLEAVED) {
+            const unsigned a = compact_bits((unsigned long long)idx >> 1, n);
+            const unsigned b = compact_bits((unsigned long long)idx, n);
+            dense[((long long)a << n) | b] = q[idx];
+        } else {
+            dense[idx] = q[idx];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ MPO construction
+
+// Identity operator as a d = 4 "MPS" (index t*2 + s), bond 1, left canonical:
+// sites 0..n-2 hold (1,0,0,1)/sqrt(2), the last site (1,0,0,1) * 2^((n-1)/2).
+__global__ void k_identity_mpo_state(float2* __restrict__ sites, int* __restrict__ bond, int n, int cap) {
+    const int p = blockIdx.x;
+    if (p >= n) return;
+    float2* s = sites + (long long)p * cap * 4 * cap;
+    const float v = (p < n - 1) ? 0.70710678118654752f : (float)pow(2.0, 0.5 * (n - 1));
+    if (threadIdx.x < 4) {
+        const int t = threadIdx.x >> 1, u = threadIdx.x & 1;
+        s[(long long)threadIdx.x * cap] = make_float2(t == u ? v : 0.f, 0.f);
+    }
+    if (threadIdx.x == 0) {
+        bond[p] = 1;
+        if (p == n - 1) bond[n] = 1;
+    }
+}
+
+// Layer j of the swap-free QFT circuit (H on qubit j, then controlled phases exp(i pi b s / 2^(k-j)) with
+// every qubit k > j, the post-H bit b carried on a bond of size 2) as an MPO on n sites.
+__global__ void k_qft_layer(float2* __restrict__ W, int* __restrict__ bond, int n, int j, int wcap) {
+    const int p = blockIdx.x;
+    if (p >= n) return;
+    float2* c = W + (long long)p * wcap * 4 * wcap;
+    const float h = 0.70710678118654752f;
+    if (threadIdx.x == 0) {
+        for (int e = 0; e < wcap * 4 * wcap; ++e) c[e] = make_float2(0.f, 0.f);
+        if (p < j) {
+            c[((0 * 2 + 0) * 2 + 0) * wcap + 0] = make_float2(1.f, 0.f);
+            c[((0 * 2 + 1) * 2 + 1) * wcap + 0] = make_float2(1.f, 0.f);
+        } else if (p == j) {
+            const int wr = (j < n - 1) ? 2 : 1;
+            for (int b = 0; b < 2; ++b)
+                for (int s = 0; s < 2; ++s) {
+                    const float hv = (b == 1 && s == 1) ? -h : h;
+                    c[((0 * 2 + b) * 2 + s) * wcap + (wr == 2 ? b : 0)] = make_float2(hv, 0.f);
+                }
+        } else {
+            const int wr = (p < n - 1) ? 2 : 1;
+            for (int b = 0; b < 2; ++b)
+                for (int s = 0; s < 2; ++s) {
+                    double sn, cs;
+                    sincospi((double)(b * s) / (double)(1ll << (p - j)), &sn, &cs);
+                    c[((b * 2 + s) * 2 + s) * wcap + (wr == 2 ? b : 0)] = make_float2((float)cs, (float)sn);
+                }
+        }
+        const int wl = (p <= j) ? 1 : 2;
+        const int wr = (p < j) ? 1 : ((p < n - 1) ? 2 : 1);
+        bond[p] = wl;
+        if (p == n - 1) bond[n] = wr;
+    }
+}
+
+// Fresnel transfer function on the grid, indexed by the site-ordered flat index (bit reversed if asked):
+// exp(-i pi c k_f^2 / L), k_f the signed fftfreq integer.  Phase reduced modulo 2 in FP64 before sincospi.
+__global__ void k_phase_vector(float2* __restrict__ v, int n, double c, int bit_reversed) {
+    const long long L = 1ll << n;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < L;
+         idx += (long long)gridDim.x * blockDim.x) {
+        long long k = idx;
+        if (bit_reversed) k = (long long)(__brevll((unsigned long long)idx) >> (64 - n));
+        const long long kf = (k < L / 2) ? k : k - L;
+        // phase / pi = -c kf^2 / L, reduced modulo 2 exactly enough in FP64
+        double e = c * (double)kf * (double)kf / (double)L;
+        e = fmod(e, 2.0);
+        double s, co;
+        sincospi(-e, &s, &co);
+        v[idx] = make_float2((float)co, (float)s);
+    }
+}
+
+// Diagonal MPO from a d = 2 MPS: W[a, t, s, b] = delta(t, s) A[a, s, b].
+__global__ void k_diag_mpo(const float2* __restrict__ A, int acap, const int* __restrict__ abond,
+                           float2* __restrict__ W, int wcap, int* __restrict__ wbond, int n) {
+    const int p = blockIdx.x;
+    if (p >= n) return;
+    const int bl = abond[p], br = abond[p + 1];
+    const float2* a = A + (long long)p * acap * 2 * acap;
+    float2* w = W + (long long)p * wcap * 4 * wcap;
+    for (int e = threadIdx.x; e < bl * 4 * br; e += blockDim.x) {
+        const int l = e / (4 * br), ts = (e / br) % 4, r = e % br;
+        const int t = ts >> 1, s = ts & 1;
+        w[((long long)l * 4 + ts) * wcap + r] = (t == s) ? a[((long long)l * 2 + s) * acap + r] : make_float2(0.f, 0.f);
+    }
+    if (threadIdx.x == 0) {
+        wbond[p] = bl;
+        if (p == n - 1) wbond[n] = br;
+    }
+}
+
+// Hermitian conjugate of MPO cores: out[a, t, s, b] = conj(in[a, s, t, b]).
+__global__ void k_mpo_dagger(const float2* __restrict__ in, const int* __restrict__ ibond, int icap,
+                             float2* __restrict__ out, int* __restrict__ obond, int ocap, int n) {
+    const int p = blockIdx.x;
+    if (p >= n) return;
+    const int bl = ibond[p], br = ibond[p + 1];
+    const float2* a = in + (long long)p * icap * 4 * icap;
+    float2* w = out + (long long)p * ocap * 4 * ocap;
+    for (int e = threadIdx.x; e < bl * 4 * br; e += blockDim.x) {
+        const int l = e / (4 * br), ts = (e / br) % 4, r = e % br;
+        const int t = ts >> 1, s = ts & 1;
+        w[((long long)l * 4 + ts) * ocap + r] = cconj(a[((long long)l * 4 + s * 2 + t) * icap + r]);
+    }
+    if (threadIdx.x == 0) {
+        obond[p] = bl;
+        if (p == n - 1) obond[n] = br;
+    }
+}
+
+// ------------------------------------------------------------------ amplitudes and overlaps
+
+// psi[digits] for `count` digit strings: one warp per string, row vector times site matrices.
+__global__ void k_amplitudes(const float2* __restrict__ sites, const int* __restrict__ bond, int N, int d, int cap,
+                             const int* __restrict__ digits, int count, float2* __restrict__ out,
+                             float2* __restrict__ scratch) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= count) return;
+    float2* v = scratch + (long long)warp * 2 * cap;
+    float2* vn = v + cap;
+    if (lane == 0) v[0] = make_float2(1.f, 0.f);
+    __syncwarp();
+    for (int p = 0; p < N; ++p) {
+        const int bl = bond[p], br = bond[p + 1];
+        const int s = digits[(long long)warp * N + p];
+        const float2* A = sites + (long long)p * cap * d * cap;
+        for (int r = lane; r < br; r += 32) {
+            float2 acc = make_float2(0.f, 0.f);
+            for (int l = 0; l < bl; ++l) cfma(acc, v[l], A[((long long)l * d + s) * cap + r]);
+            vn[r] = acc;
+        }
+        __syncwarp();
+        for (int r = lane; r < br; r += 32) v[r] = vn[r];
+        __syncwarp();
+    }
+    if (lane == 0) out[warp] = v[0];
+}
+
+// Left transfer-matrix step of <a|b>: E'[k, l] = sum_{i, j, s} conj(A[i, s, k]) E[i, j] B[j, s, l], FP64 E.
+// One block per output row k; threads over l.
+__global__ void k_transfer_step(const double2* __restrict__ E, int lde, const float2* __restrict__ A, int acap,
+                                int abl, int abr, const float2* __restrict__ B, int bcap, int bbl, int bbr, int d,
+                                double2* __restrict__ En) {
+    const int k = blockIdx.x;
+    if (k >= abr) return;
+    for (int l = threadIdx.x; l < bbr; l += blockDim.x) {
+        double re = 0.0, im = 0.0;
+        for (int s = 0; s < d; ++s) {
+            for (int j = 0; j < bbl; ++j) {
+                // t_j = sum_i conj(A[i, s, k]) E[i, j]
+                double tr = 0.0, ti = 0.0;
+                for (int i = 0; i < abl; ++i) {
+                    const float2 a = A[((long long)i * d + s) * acap + k];
+                    const double2 e = E[(long long)i * lde + j];
+                    tr += (double)a.x * e.x + (double)a.y * e.y;
+                    ti += (double)a.x * e.y - (double)a.y * e.x;
+                }
+                const float2 b = B[((long long)j * d + s) * bcap + l];
+                re += tr * b.x - ti * b.y;
+                im += tr * b.y + ti * b.x;
+            }
+        }
+        En[(long long)k * lde + l] = make_double2(re, im);
+    }
+}
+
+}  // namespace qtn

@@ -1,0 +1,769 @@
+// C ABI of the quantics tensor-network Fresnel library: host-side orchestration.
+//
+// Every entry point only enqueues kernels on the context's stream.  Sizes that
+// depend on truncation are carried in device dimension registers (see
+// qtn_internal.cuh), so the host never waits for a bond dimension.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "qtn_internal.cuh"
+
+namespace qtn {
+
+// kernels from k_mps.cu
+__global__ void k_plan_site(const int*, const int*, int, int, int, int, int, int, int*);
+__global__ void k_plan_encode(int, int, int*);
+__global__ void k_reset_stats(int*, double*);
+__global__ void k_stage2(const float2*, float2*, const float2*, int, int, int, int, const int*);
+__global__ void k_trace(const double2*, int, Dim, const int*, double*);
+__global__ void k_row_weights(const float2*, Dim, Dim, Dim, double*, const int*);
+__global__ void k_select(const double*, Dim, int, double, int, int*, int*, double*);
+__global__ void k_write_site(const float2*, int, const int*, float2*, int, int, int, int*, int, const int*);
+__global__ void k_gather_rows(const float2*, Dim, const int*, float2*, Dim, Dim, const int*);
+__global__ void k_write_last(const float2*, float2*, int, int, int, const int*);
+__global__ void k_site_norm2(const float2*, int, int, const int*, int, double*, int);
+__global__ void k_to_f32(const double2*, float2*, int, Dim, const int*);
+__global__ void k_whiten(float2*, int, const double*, Dim, double, const int*);
+__global__ void k_dense_to_quantics(const float2*, float2*, int, int);
+__global__ void k_quantics_to_dense(const float2*, float2*, int, int);
+__global__ void k_identity_mpo_state(float2*, int*, int, int);
+__global__ void k_qft_layer(float2*, int*, int, int, int);
+__global__ void k_phase_vector(float2*, int, double, int);
+__global__ void k_diag_mpo(const float2*, int, const int*, float2*, int, int*, int);
+__global__ void k_mpo_dagger(const float2*, const int*, int, float2*, int*, int, int);
+__global__ void k_amplitudes(const float2*, const int*, int, int, int, const int*, int, float2*, float2*);
+__global__ void k_transfer_step(const double2*, int, const float2*, int, int, int, const float2*, int, int, int, int,
+                                double2*);
+
+// small helper kernels local to this file
+__global__ void k_set_one(float2* p) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) p[0] = make_float2(1.f, 0.f);
+}
+__global__ void k_set_boundary(int* bond, int N) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) { bond[0] = 1; bond[N] = 1; }
+}
+__global__ void k_set_reg(int* R, int reg, int v) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) R[reg] = v;
+}
+__global__ void k_plan_dense(const int* bond, int p, int d, int* R) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        R[R_TMP0] = bond[p];
+        R[R_TMP1] = bond[p + 1];
+        R[R_TMP2] = d * bond[p + 1];
+    }
+}
+__global__ void k_copy_ledger_out(const double* ledger, const int* R, double* out_d, int* out_i) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        for (int i = 0; i < L_COUNT; ++i) out_d[i] = ledger[i];
+        out_i[0] = R[R_SWEEPS];
+        out_i[1] = R[R_FLAGS];
+        out_i[2] = R[R_MAXBOND];
+    }
+}
+
+// ------------------------------------------------------------------ workspace layout
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+WsLayout ws_layout(int N, int d, int chi, int w, long long dense) {
+    WsLayout L{};
+    L.n_sites = N;
+    L.chi = chi;
+    L.d = d;
+    L.w = w;
+    L.m_cap = d * chi;
+    L.n_cap = std::max(w, 1) * chi;
+    L.p_cap = EIG_MAX;
+    L.dense = dense;
+    const size_t c8 = sizeof(float2), c16 = sizeof(double2);
+    const size_t mc = (size_t)L.m_cap, nc = (size_t)L.n_cap, pc = (size_t)L.p_cap;
+    const size_t gdim = std::max(mc, pc);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+    L.ledger = take(L_COUNT * sizeof(double) + 64 * sizeof(int));
+    L.regs = take(R_COUNT * sizeof(int) + (2 * gdim + 1024) * sizeof(int));   // registers, perm, tmp bonds
+    L.T = take(mc * nc * c8);
+    L.P = take((size_t)chi * std::max(w, 1) * d * chi * c8);
+    L.carry = take((size_t)chi * nc * c8 + c8);
+    L.G64 = take(gdim * gdim * c16);
+    L.G32 = take(gdim * gdim * c8);
+    L.U = take(gdim * gdim * c8);
+    L.lam = take(4 * gdim * sizeof(double));
+    L.Y = take(gdim * pc * c8);
+    L.Q = take(gdim * pc * c8);
+    L.S64 = take(gdim * gdim * c16);
+    L.Z = take(std::max(gdim * nc, pc * pc) * c8);   // projected rows X = U^dagger T (zip-up)
+    L.omega = take((size_t)N * chi * d * chi * c8 + (size_t)N * 64 * c8);   // MPS-sized scratch + layer MPO
+    const size_t dn = (size_t)std::max<long long>(dense, 1);
+    L.X0 = take(dn * c8);
+    L.X1 = take(dn * c8);
+    L.total = off;
+    return L;
+}
+
+static Ws ws_bind(void* base, const WsLayout& L) {
+    char* b = (char*)base;
+    Ws w;
+    w.L = L;
+    w.ledger = (double*)(b + L.ledger);
+    w.R = (int*)(b + L.regs);
+    w.T = (float2*)(b + L.T);
+    w.P = (float2*)(b + L.P);
+    w.carry = (float2*)(b + L.carry);
+    w.G64 = (double2*)(b + L.G64);
+    w.G32 = (float2*)(b + L.G32);
+    w.U = (float2*)(b + L.U);
+    w.lam = (double*)(b + L.lam);
+    w.Y = (float2*)(b + L.Y);
+    w.Q = (float2*)(b + L.Q);
+    w.S64 = (double2*)(b + L.S64);
+    w.Z = (float2*)(b + L.Z);
+    w.X0 = (float2*)(b + L.X0);
+    w.X1 = (float2*)(b + L.X1);
+    return w;
+}
+
+// extra int scratch after the registers: perm[gdim], tmp bonds[...]
+static int* ws_perm(Ws& w) { return w.R + R_COUNT; }
+static int* ws_tmpbond(Ws& w) { return w.R + R_COUNT + 2 * std::max(w.L.m_cap, w.L.p_cap); }
+static double* ws_weights(Ws& w) { return w.lam + std::max(w.L.m_cap, w.L.p_cap); }
+static double* ws_lam2(Ws& w) { return w.lam + 2 * std::max(w.L.m_cap, w.L.p_cap); }
+static float2* ws_mtmp(void* base, const WsLayout& L) { return (float2*)((char*)base + L.omega); }
+
+#define CK(expr)                                                      \
+    do {                                                              \
+        cudaError_t _e = (expr);                                      \
+        if (_e != cudaSuccess) {                                      \
+            fprintf(stderr, "qtn: CUDA error %s at %s:%d\n", cudaGetErrorString(_e), __FILE__, __LINE__); \
+            return QTN_ERR_CUDA;                                      \
+        }                                                             \
+    } while (0)
+#define CKL() CK(cudaGetLastError())
+
+// Relative weight below which a direction of an untruncated (gauge-only) sweep is FP32 round-off.
+constexpr double EXACT_CUTOFF = 1e-13;
+
+static int grid_for(long long n, int threads, int sm) {
+    long long g = (n + threads - 1) / threads;
+    long long cap = (long long)sm * 8;
+    return (int)std::max(1LL, std::min(g, cap));
+}
+
+// ------------------------------------------------------------------ truncated SVD of T (m x n, row stride n)
+//
+// 1. G = T T^dagger, FP32 products accumulated in FP64 (split-K atomics).
+// 2. Eigenbasis U of G: one-sided Jacobi in shared memory when m <= EIG_MAX; otherwise a randomised
+//    range finder with power iterations and a Rayleigh-Ritz step on an EIG_MAX-dimensional subspace.
+// 3. X = U^dagger T; row weights |x_i|^2 (FP64) are the captured weights of every direction; the
+//    truncation rule runs on them with total = trace(G).  The kept columns of U become the new
+//    site and the kept rows of X the carry.
+struct TsvdIO {
+    const float2* T;     // input, row stride R_N
+    Dim m, n;            // live dims
+    int m_cap;           // capacity of m (host)
+    long long n_cap;     // capacity of n (host)
+    float2* X;           // output rows U^dagger T, row stride R_N, capacity m_cap x n_cap (or p x n)
+};
+
+static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int chi_cap_out, Dim& rows_out) {
+    cudaStream_t s = c->stream;
+    const int mc = io.m_cap;
+    const int gld = std::max(w.L.m_cap, w.L.p_cap);
+    CK(cudaMemsetAsync(w.G64, 0, (size_t)mc * gld * sizeof(double2), s));
+    {
+        GemmDesc g{};
+        g.A = mat(io.T, io.n, dc(1));
+        g.B = mat(io.T, dc(1), io.n, 1);
+        g.C = w.G64; g.crs = dc(gld); g.ccs = dc(1);
+        g.M = io.m; g.N = io.m; g.K = io.n;
+        g.mode = OUT_ATOMIC64;
+        int tiles = ((mc + 63) / 64) * ((mc + 63) / 64);
+        long long want = std::max(1, (c->sm_count * 4) / std::max(tiles, 1));
+        long long kc = std::max<long long>(256, (io.n_cap + want - 1) / want);
+        kc = (kc + 15) / 16 * 16;
+        g.kchunk = (int)std::min<long long>(kc, 1 << 30);
+        g.alpha_re = 1.f; g.omega_seed = -1;
+        CK(launch_gemm(g, mc, mc, (int)std::min<long long>(io.n_cap, 1 << 30), w.R, s));
+    }
+    k_trace<<<1, 256, 0, s>>>(w.G64, gld, io.m, w.R, w.ledger);
+    CKL();
+    const int max_sweeps = tr.max_sweeps > 0 ? tr.max_sweeps : 30;
+    Dim rows;
+    if (mc <= EIG_MAX) {
+        CK(launch_eig(w.G64, dc(gld), io.m, w.U, dc(gld), w.lam, w.R, mc, max_sweeps, w.ledger, s));
+        rows = io.m;
+    } else {
+        const int pc = w.L.p_cap;
+        Dim P = dr(R_P);
+        k_to_f32<<<grid_for((long long)mc * mc, 256, c->sm_count), 256, 0, s>>>(w.G64, w.G32, gld, io.m, w.R);
+        CKL();
+        auto gemm_G = [&](const float2* B, int seed) -> qtn_status {   // Y = G32 * B (m x p)
+            GemmDesc g{};
+            g.A = mat(w.G32, dc(gld), dc(1));
+            g.B = mat(B, dc(pc), dc(1));
+            g.C = w.Y; g.crs = dc(pc); g.ccs = dc(1);
+            g.M = io.m; g.N = P; g.K = io.m;
+            g.mode = OUT_STORE; g.alpha_re = 1.f; g.omega_seed = seed;
+            CK(launch_gemm(g, mc, pc, mc, w.R, s));
+            return QTN_OK;
+        };
+        auto gram_p = [&](const float2* A_, const float2* B_) -> qtn_status {   // S64 = A_^dagger B_ (p x p)
+            CK(cudaMemsetAsync(w.S64, 0, (size_t)pc * pc * sizeof(double2), s));
+            GemmDesc g{};
+            g.A = mat(A_, dc(1), dc(pc), 1);
+            g.B = mat(B_, dc(pc), dc(1));
+            g.C = w.S64; g.crs = dc(pc); g.ccs = dc(1);
+            g.M = P; g.N = P; g.K = io.m;
+            g.mode = OUT_ATOMIC64; g.kchunk = 64; g.alpha_re = 1.f; g.omega_seed = -1;
+            CK(launch_gemm(g, pc, pc, mc, w.R, s));
+            return QTN_OK;
+        };
+        auto orth = [&]() -> qtn_status {   // Q = Y (Y^dagger Y)^{-1/2} through the eigenbasis of Y^dagger Y
+            qtn_status st = gram_p(w.Y, w.Y);
+            if (st) return st;
+            CK(launch_eig(w.S64, dc(pc), P, w.Z, dc(pc), ws_lam2(w), w.R, pc, max_sweeps, w.ledger, s));
+            k_whiten<<<grid_for((long long)pc * pc, 256, c->sm_count), 256, 0, s>>>(w.Z, pc, ws_lam2(w), P, 1e-9, w.R);
+            CKL();
+            GemmDesc g{};
+            g.A = mat(w.Y, dc(pc), dc(1));
+            g.B = mat(w.Z, dc(1), dc(pc));
+            g.C = w.Q; g.crs = dc(pc); g.ccs = dc(1);
+            g.M = io.m; g.N = P; g.K = P;
+            g.mode = OUT_STORE; g.alpha_re = 1.f; g.omega_seed = -1;
+            CK(launch_gemm(g, mc, pc, pc, w.R, s));
+            return QTN_OK;
+        };
+        qtn_status st;
+        if ((st = gemm_G(nullptr, 7919))) return st;
+        if ((st = orth())) return st;
+        const int power_iters = 2;
+        for (int it = 0; it < power_iters; ++it) {
+            if ((st = gemm_G(w.Q, -1))) return st;
+            if ((st = orth())) return st;
+        }
+        // Rayleigh-Ritz: H = Q^dagger G Q, eigenbasis Z, Ritz vectors U = Q Z (column-major, ld gld)
+        if ((st = gemm_G(w.Q, -1))) return st;
+        if ((st = gram_p(w.Q, w.Y))) return st;
+        CK(launch_eig(w.S64, dc(pc), P, w.Z, dc(pc), w.lam, w.R, pc, max_sweeps, w.ledger, s));
+        GemmDesc g{};
+        g.A = mat(w.Q, dc(pc), dc(1));
+        g.B = mat(w.Z, dc(1), dc(pc));
+        g.C = w.U; g.crs = dc(1); g.ccs = dc(gld);
+        g.M = io.m; g.N = P; g.K = P;
+        g.mode = OUT_STORE; g.alpha_re = 1.f; g.omega_seed = -1;
+        CK(launch_gemm(g, mc, pc, pc, w.R, s));
+        rows = P;
+    }
+    // X = U^dagger T  (rows x n)
+    {
+        GemmDesc g{};
+        g.A = mat(w.U, dc(gld), dc(1), 1);
+        g.B = mat(io.T, io.n, dc(1));
+        g.C = io.X; g.crs = io.n; g.ccs = dc(1);
+        g.M = rows; g.N = io.n; g.K = io.m;
+        g.mode = OUT_STORE; g.alpha_re = 1.f; g.omega_seed = -1;
+        const int max_rows = (mc <= EIG_MAX) ? mc : w.L.p_cap;
+        CK(launch_gemm(g, max_rows, (int)std::min<long long>(io.n_cap, 1 << 30), mc, w.R, s));
+    }
+    k_row_weights<<<grid_for((long long)gld * 32, 256, c->sm_count), 256, 0, s>>>(io.X, io.n, rows, io.n,
+                                                                                    ws_weights(w), w.R);
+    CKL();
+    k_select<<<1, 256, 0, s>>>(ws_weights(w), rows, tr.chi_max, tr.cutoff, chi_cap_out, ws_perm(w), w.R, w.ledger);
+    CKL();
+    rows_out = rows;
+    return QTN_OK;
+}
+
+// ------------------------------------------------------------------ one zip-up sweep
+static qtn_status zip_pass(Ctx* c, Ws& w, qtn_mps* psi, const qtn_mpo* W, int axis, int moff, int mn, int mirror,
+                           const qtn_trunc& tr) {
+    cudaStream_t s = c->stream;
+    const int N = psi->n_sites, d = psi->d, cap = psi->chi_cap;
+    const int wcap = W ? W->w_cap : 1, wmax = W ? std::max(W->w_max, 1) : 1;
+    if (d * cap > w.L.m_cap || wmax * cap > w.L.n_cap || wmax > std::max(w.L.w, 1)) return QTN_ERR_WORKSPACE;
+    float2* sites = (float2*)psi->sites;
+    const size_t sstride = (size_t)cap * d * cap;
+    k_set_one<<<1, 1, 0, s>>>(w.carry);
+    CKL();
+    qtn_trunc t2 = tr;
+    if (t2.chi_max <= 0 || t2.chi_max > cap) t2.chi_max = cap;
+    for (int p = 0; p < N; ++p) {
+        const int q = mirror ? N - 1 - p : p;
+        float2* site_q = sites + (size_t)q * sstride;
+        k_plan_site<<<1, 1, 0, s>>>(psi->bond, W ? W->bond : nullptr, N, d, mirror, moff, mn, p, w.R);
+        CKL();
+        {   // P[(x a), (t k)] = sum_j carry[(x a), j] A_q[j, t, k]
+            GemmDesc g{};
+            g.A = mat(w.carry, dr(R_CHIL), dc(1));
+            g.B = mirror ? mat2(site_q, dc(1), dr(R_CHIR), dc(cap), dc(d * cap))
+                         : mat2(site_q, dc(d * cap), dr(R_CHIR), dc(cap), dc(1));
+            g.C = w.P; g.crs = dr(R_DN); g.ccs = dc(1);
+            g.M = dr(R_MID); g.N = dr(R_DN); g.K = dr(R_CHIL);
+            g.mode = OUT_STORE; g.alpha_re = 1.f; g.omega_seed = -1;
+            CK(launch_gemm(g, cap * wmax, d * cap, cap, w.R, s));
+        }
+        const float2* Wc = nullptr;
+        const int qm = q - moff;
+        if (W && qm >= 0 && qm < mn) Wc = (const float2*)W->sites + (size_t)qm * wcap * 4 * wcap;
+        k_stage2<<<grid_for((long long)d * cap * wmax * cap, 256, c->sm_count), 256, 0, s>>>(w.P, w.T, Wc, wcap,
+                                                                                             mirror, d, axis, w.R);
+        CKL();
+        if (p == N - 1) {
+            k_write_last<<<1, 256, 0, s>>>(w.T, site_q, cap, d, mirror, w.R);
+            CKL();
+            break;
+        }
+        TsvdIO io{w.T, dr(R_M), dr(R_N), d * cap, (long long)wmax * cap, w.Z};
+        Dim rows;
+        qtn_status st = tsvd(c, w, io, t2, cap, rows);
+        if (st) return st;
+        const int gld = std::max(w.L.m_cap, w.L.p_cap);
+        k_write_site<<<grid_for((long long)cap * d * cap, 256, c->sm_count), 256, 0, s>>>(
+            w.U, gld, ws_perm(w), site_q, cap, d, mirror, psi->bond, mirror ? q : q + 1, w.R);
+        CKL();
+        k_gather_rows<<<grid_for((long long)cap * wmax * cap, 256, c->sm_count), 256, 0, s>>>(
+            w.Z, dr(R_N), ws_perm(w), w.carry, dr(R_N), dr(R_N), w.R);
+        CKL();
+    }
+    const int qlast = mirror ? 0 : N - 1;
+    k_site_norm2<<<1, 512, 0, s>>>(sites + (size_t)qlast * sstride, cap, d, psi->bond, qlast, w.ledger, L_NORM2);
+    CKL();
+    psi->canon = mirror ? QTN_CANON_RIGHT : QTN_CANON_LEFT;
+    return QTN_OK;
+}
+
+static qtn_status fill_stats(Ctx* c, Ws& w, qtn_stats* st) {
+    if (!st) return QTN_OK;
+    double hd[L_COUNT];
+    int hi[4];
+    CK(cudaMemcpyAsync(hd, w.ledger, sizeof(hd), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(hi, w.R + R_SWEEPS, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    st->discarded = hd[L_DISCARDED];
+    st->norm2 = hd[L_NORM2];
+    st->sweeps_used = hi[0];
+    st->flags = hi[1];
+    st->max_bond = hi[2];
+    if (hi[1] & 4) return QTN_ERR_NONFINITE;
+    return QTN_OK;
+}
+
+static qtn_status check_ws(const WsLayout& need, void* ws, size_t bytes) {
+    if (!ws) return QTN_ERR_WORKSPACE;
+    if (bytes < need.total) return QTN_ERR_WORKSPACE;
+    return QTN_OK;
+}
+
+static int mps_layout_n(const qtn_mps* psi, qtn_layout layout) {
+    if (layout == QTN_LAYOUT_INTERLEAVED) return psi->n_sites;
+    if (layout == QTN_LAYOUT_SERIAL) return psi->n_sites / 2;
+    return psi->n_sites;
+}
+
+}  // namespace qtn
+
+using namespace qtn;
+
+// ============================================================================ C ABI
+
+struct qtn_context {
+    Ctx c;
+    WsLayout L;        // layout of the workspace the caller sized with qtn_workspace_size
+    int have_layout;
+};
+
+static qtn_status bind_ws(qtn_context* x, void* ws, size_t bytes, Ws& w) {
+    if (!x->have_layout) return QTN_ERR_WORKSPACE;
+    qtn_status st = check_ws(x->L, ws, bytes);
+    if (st) return st;
+    w = ws_bind(ws, x->L);
+    return QTN_OK;
+}
+
+extern "C" {
+
+int qtn_version(void) { return 1; }
+
+const char* qtn_status_string(qtn_status s) {
+    switch (s) {
+        case QTN_OK: return "ok";
+        case QTN_ERR_ARG: return "invalid argument";
+        case QTN_ERR_SHAPE: return "inconsistent shapes";
+        case QTN_ERR_CAPACITY: return "capacity exceeded";
+        case QTN_ERR_NOCONV: return "eigen-solve did not converge";
+        case QTN_ERR_NONFINITE: return "non-finite value";
+        case QTN_ERR_TIMEOUT: return "bounded device wait gave up";
+        case QTN_ERR_CUDA: return "CUDA runtime error";
+        case QTN_ERR_BOUNDS: return "index out of bounds";
+        case QTN_ERR_WORKSPACE: return "workspace missing or too small";
+    }
+    return "unknown status";
+}
+
+qtn_status qtn_create(void** ctx, void* stream) {
+    if (!ctx) return QTN_ERR_ARG;
+    qtn_context* x = (qtn_context*)calloc(1, sizeof(qtn_context));
+    if (!x) return QTN_ERR_ARG;
+    x->c.stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&x->c.device) != cudaSuccess) { free(x); return QTN_ERR_CUDA; }
+    if (cudaDeviceGetAttribute(&x->c.sm_count, cudaDevAttrMultiProcessorCount, x->c.device) != cudaSuccess) {
+        free(x);
+        return QTN_ERR_CUDA;
+    }
+    *ctx = x;
+    return QTN_OK;
+}
+
+qtn_status qtn_destroy(void* ctx) {
+    free(ctx);
+    return QTN_OK;
+}
+
+qtn_status qtn_set_stream(void* ctx, void* stream) {
+    if (!ctx) return QTN_ERR_ARG;
+    ((qtn_context*)ctx)->c.stream = (cudaStream_t)stream;
+    return QTN_OK;
+}
+
+qtn_status qtn_workspace_size(void* ctx, int n_sites, int d, int chi_max, int w_max, long long dense_elems,
+                              size_t* bytes) {
+    if (!ctx || !bytes || n_sites < 1 || (d != 2 && d != 4) || chi_max < 1 || w_max < 1 || dense_elems < 0)
+        return QTN_ERR_ARG;
+    qtn_context* x = (qtn_context*)ctx;
+    x->L = ws_layout(n_sites, d, chi_max, w_max, dense_elems);
+    x->have_layout = 1;
+    *bytes = x->L.total;
+    return QTN_OK;
+}
+
+qtn_status qtn_encode(void* ctx, const void* dense, int n, qtn_layout layout, qtn_trunc trunc, qtn_mps* out,
+                      qtn_stats* stats, void* ws, size_t ws_bytes) {
+    if (!ctx || !dense || !out || n < 1 || n > 30) return QTN_ERR_ARG;
+    if (layout < QTN_LAYOUT_SERIAL || layout > QTN_LAYOUT_1D) return QTN_ERR_ARG;
+    qtn_context* x = (qtn_context*)ctx;
+    Ws w;
+    qtn_status st = bind_ws(x, ws, ws_bytes, w);
+    if (st) return st;
+    const int N = layout == QTN_LAYOUT_INTERLEAVED ? n : (layout == QTN_LAYOUT_SERIAL ? 2 * n : n);
+    const int d = layout == QTN_LAYOUT_INTERLEAVED ? 4 : 2;
+    if (out->n_sites != N || out->d != d) return QTN_ERR_SHAPE;
+    const long long total = layout == QTN_LAYOUT_1D ? (1ll << n) : (1ll << (2 * n));
+    if (total > w.L.dense || d * out->chi_cap > w.L.m_cap) return QTN_ERR_WORKSPACE;
+    Ctx* c = &x->c;
+    cudaStream_t s = c->stream;
+    k_reset_stats<<<1, 1, 0, s>>>(w.R, w.ledger);
+    k_set_boundary<<<1, 1, 0, s>>>(out->bond, N);
+    k_dense_to_quantics<<<grid_for(total, 256, c->sm_count), 256, 0, s>>>((const float2*)dense, w.X0, n, layout);
+    CKL();
+    qtn_trunc t2 = trunc;
+    if (t2.chi_max <= 0 || t2.chi_max > out->chi_cap) t2.chi_max = out->chi_cap;
+    const int cap = out->chi_cap;
+    const size_t sstride = (size_t)cap * d * cap;
+    float2* cur = w.X0;
+    float2* nxt = w.X1;
+    long long ncols = total / d;
+    for (int p = 0; p < N - 1; ++p) {
+        k_plan_encode<<<1, 1, 0, s>>>(p, d, w.R);
+        k_set_reg<<<1, 1, 0, s>>>(w.R, R_N, (int)ncols);
+        CKL();
+        TsvdIO io{cur, dr(R_M), dr(R_N), d * cap, ncols, nxt};
+        Dim rows;
+        st = tsvd(c, w, io, t2, cap, rows);
+        if (st) return st;
+        const int gld = std::max(w.L.m_cap, w.L.p_cap);
+        k_write_site<<<grid_for((long long)cap * d * cap, 256, c->sm_count), 256, 0, s>>>(
+            w.U, gld, ws_perm(w), (float2*)out->sites + (size_t)p * sstride, cap, d, 0, out->bond, p + 1, w.R);
+        k_gather_rows<<<grid_for((long long)cap * ncols, 256, c->sm_count), 256, 0, s>>>(nxt, dr(R_N), ws_perm(w),
+                                                                                          cur, dr(R_N), dr(R_N), w.R);
+        CKL();
+        ncols /= d;
+    }
+    k_plan_encode<<<1, 1, 0, s>>>(N - 1, d, w.R);
+    k_write_last<<<1, 256, 0, s>>>(cur, (float2*)out->sites + (size_t)(N - 1) * sstride, cap, d, 0, w.R);
+    k_site_norm2<<<1, 512, 0, s>>>((float2*)out->sites + (size_t)(N - 1) * sstride, cap, d, out->bond, N - 1, w.ledger,
+                                   L_NORM2);
+    CKL();
+    out->canon = QTN_CANON_LEFT;
+    return fill_stats(c, w, stats);
+}
+
+// Internal: zip-up application without resetting the statistics.
+static qtn_status apply_inner(qtn_context* x, Ws& w, const qtn_mpo* W, int axis, qtn_mps* psi, const qtn_trunc& tr) {
+    const int d = psi->d, N = psi->n_sites;
+    int moff = 0, mn = N;
+    if (W) {
+        mn = W->n_sites;
+        if (d == 4) {
+            if (N != mn) return QTN_ERR_SHAPE;
+            if (axis != 0 && axis != 1) return QTN_ERR_ARG;
+        } else if (N == mn) {
+            axis = 0;
+        } else if (N == 2 * mn) {
+            if (axis != 0 && axis != 1) return QTN_ERR_ARG;
+            moff = axis * mn;
+        } else {
+            return QTN_ERR_SHAPE;
+        }
+    }
+    qtn_status st;
+    if (psi->canon == QTN_CANON_NONE) {
+        qtn_trunc exact = tr;
+        exact.chi_max = psi->chi_cap;
+        exact.cutoff = EXACT_CUTOFF;
+        st = zip_pass(&x->c, w, psi, nullptr, 0, 0, N, 0, exact);
+        if (st) return st;
+    }
+    const int mirror = (psi->canon == QTN_CANON_LEFT) ? 1 : 0;
+    return zip_pass(&x->c, w, psi, W, axis, moff, mn, mirror, tr);
+}
+
+qtn_status qtn_apply_mpo(void* ctx, const qtn_mpo* W, int axis, qtn_mps* psi, qtn_trunc trunc, qtn_stats* stats,
+                         void* ws, size_t ws_bytes) {
+    if (!ctx || !W || !psi) return QTN_ERR_ARG;
+    qtn_context* x = (qtn_context*)ctx;
+    Ws w;
+    qtn_status st = bind_ws(x, ws, ws_bytes, w);
+    if (st) return st;
+    k_reset_stats<<<1, 1, 0, x->c.stream>>>(w.R, w.ledger);
+    st = apply_inner(x, w, W, axis, psi, trunc);
+    if (st) return st;
+    return fill_stats(&x->c, w, stats);
+}
+
+qtn_status qtn_truncate(void* ctx, qtn_mps* psi, qtn_trunc trunc, qtn_stats* stats, void* ws, size_t ws_bytes) {
+    if (!ctx || !psi) return QTN_ERR_ARG;
+    qtn_context* x = (qtn_context*)ctx;
+    Ws w;
+    qtn_status st = bind_ws(x, ws, ws_bytes, w);
+    if (st) return st;
+    k_reset_stats<<<1, 1, 0, x->c.stream>>>(w.R, w.ledger);
+    if (psi->canon != QTN_CANON_LEFT) {
+        qtn_trunc exact = trunc;
+        exact.chi_max = psi->chi_cap;
+        exact.cutoff = EXACT_CUTOFF;
+        st = zip_pass(&x->c, w, psi, nullptr, 0, 0, psi->n_sites, 0, exact);
+        if (st) return st;
+        // the exact sweep discards nothing of substance; keep its FP32 round-off out of the report
+        CK(cudaMemsetAsync(w.ledger + L_DISCARDED, 0, sizeof(double), x->c.stream));
+    }
+    st = zip_pass(&x->c, w, psi, nullptr, 0, 0, psi->n_sites, 1, trunc);
+    if (st) return st;
+    return fill_stats(&x->c, w, stats);
+}
+
+qtn_status qtn_fresnel_step(void* ctx, qtn_mps* psi, qtn_layout layout, const qtn_mpo* qft, const qtn_mpo* qft_dagger,
+                            const qtn_mpo* phase, int n_steps, qtn_trunc trunc, qtn_stats* stats, void* ws,
+                            size_t ws_bytes) {
+    if (!ctx || !psi || !qft || !qft_dagger || !phase || n_steps < 0) return QTN_ERR_ARG;
+    qtn_context* x = (qtn_context*)ctx;
+    Ws w;
+    qtn_status st = bind_ws(x, ws, ws_bytes, w);
+    if (st) return st;
+    k_reset_stats<<<1, 1, 0, x->c.stream>>>(w.R, w.ledger);
+    const int naxes = (layout == QTN_LAYOUT_1D) ? 1 : 2;
+    const qtn_mpo* ops[3] = {qft, phase, qft_dagger};
+    for (int step = 0; step < n_steps; ++step)
+        for (int o = 0; o < 3; ++o)
+            for (int ax = 0; ax < naxes; ++ax) {
+                st = apply_inner(x, w, ops[o], ax, psi, trunc);
+                if (st) return st;
+            }
+    return fill_stats(&x->c, w, stats);
+}
+
+qtn_status qtn_build_qft_mpo(void* ctx, int n, int inverse, double cutoff, qtn_mpo* out, void* ws, size_t ws_bytes) {
+    if (!ctx || !out || n < 1 || out->n_sites != n || out->w_cap < 2) return QTN_ERR_ARG;
+    qtn_context* x = (qtn_context*)ctx;
+    Ws w;
+    qtn_status st = bind_ws(x, ws, ws_bytes, w);
+    if (st) return st;
+    cudaStream_t s = x->c.stream;
+    const int cap = out->w_cap;
+    if (4 * cap > w.L.m_cap || 2 * cap > w.L.n_cap || w.L.w < 2) return QTN_ERR_WORKSPACE;
+    float2* mt = ws_mtmp(ws, w.L);
+    if ((size_t)n * cap * 4 * cap > (size_t)w.L.n_sites * w.L.chi * w.L.d * w.L.chi || n + 1 > 900)
+        return QTN_ERR_WORKSPACE;
+    int* tb = ws_tmpbond(w);
+    float2* layer = mt + (size_t)n * cap * 4 * cap;
+    int* laybond = tb + 64;
+    qtn_mps stt{n, 4, cap, QTN_CANON_LEFT, inverse ? tb : out->bond, inverse ? (void*)mt : out->sites};
+    k_reset_stats<<<1, 1, 0, s>>>(w.R, w.ledger);
+    k_identity_mpo_state<<<n, 32, 0, s>>>((float2*)stt.sites, stt.bond, n, cap);
+    CKL();
+    qtn_trunc tr{cap, cutoff, QTN_PLAIN_FP32, 0};
+    for (int j = 0; j < n; ++j) {
+        k_qft_layer<<<n, 32, 0, s>>>(layer, laybond, n, j, 2);
+        CKL();
+        qtn_mpo L{n, 2, 2, laybond, layer};
+        const int mirror = (stt.canon == QTN_CANON_LEFT) ? 1 : 0;
+        st = zip_pass(&x->c, w, &stt, &L, 0, 0, n, mirror, tr);
+        if (st) return st;
+    }
+    if (inverse) {
+        k_mpo_dagger<<<n, 128, 0, s>>>(mt, tb, cap, (float2*)out->sites, out->bond, cap, n);
+        CKL();
+    }
+    std::vector<int> hb(n + 1);
+    CK(cudaMemcpyAsync(hb.data(), out->bond, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    out->w_max = *std::max_element(hb.begin(), hb.end());
+    return QTN_OK;
+}
+
+qtn_status qtn_build_phase_mpo(void* ctx, int n, double c, int bit_reversed, double cutoff, qtn_mpo* out, void* ws,
+                               size_t ws_bytes) {
+    if (!ctx || !out || n < 1 || n > 24 || out->n_sites != n || out->w_cap < 1) return QTN_ERR_ARG;
+    qtn_context* x = (qtn_context*)ctx;
+    Ws w;
+    qtn_status st = bind_ws(x, ws, ws_bytes, w);
+    if (st) return st;
+    cudaStream_t s = x->c.stream;
+    const int cap = out->w_cap;
+    if ((1ll << n) > w.L.dense || 2 * cap > w.L.m_cap) return QTN_ERR_WORKSPACE;
+    // the temporary d = 2 MPS lives in the MPS-sized scratch (n_sites x chi x d x chi of the sizing call)
+    if ((size_t)n * cap * 2 * cap > (size_t)w.L.n_sites * w.L.chi * w.L.d * w.L.chi) return QTN_ERR_WORKSPACE;
+    float2* mt = ws_mtmp(ws, w.L);
+    int* tb = ws_tmpbond(w);
+    k_phase_vector<<<grid_for(1ll << n, 256, x->c.sm_count), 256, 0, s>>>(w.X1, n, c, bit_reversed);
+    CKL();
+    qtn_mps tmp{n, 2, cap, QTN_CANON_NONE, tb, mt};
+    qtn_trunc tr{cap, cutoff, QTN_PLAIN_FP32, 0};
+    st = qtn_encode(ctx, w.X1, n, QTN_LAYOUT_1D, tr, &tmp, nullptr, ws, ws_bytes);
+    if (st) return st;
+    k_diag_mpo<<<n, 128, 0, s>>>(mt, cap, tb, (float2*)out->sites, cap, out->bond, n);
+    CKL();
+    std::vector<int> hb(n + 1);
+    CK(cudaMemcpyAsync(hb.data(), out->bond, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    out->w_max = *std::max_element(hb.begin(), hb.end());
+    return QTN_OK;
+}
+
+qtn_status qtn_mpo_dagger(void* ctx, const qtn_mpo* in, qtn_mpo* out) {
+    if (!ctx || !in || !out || in->n_sites != out->n_sites || out->w_cap < in->w_max) return QTN_ERR_ARG;
+    if (in->sites == out->sites) return QTN_ERR_ARG;
+    qtn_context* x = (qtn_context*)ctx;
+    k_mpo_dagger<<<in->n_sites, 128, 0, x->c.stream>>>((const float2*)in->sites, in->bond, in->w_cap,
+                                                        (float2*)out->sites, out->bond, out->w_cap, in->n_sites);
+    CKL();
+    out->w_max = in->w_max;
+    return QTN_OK;
+}
+
+qtn_status qtn_to_dense(void* ctx, const qtn_mps* psi, qtn_layout layout, void* dense, long long cap_elems, void* ws,
+                        size_t ws_bytes) {
+    if (!ctx || !psi || !dense) return QTN_ERR_ARG;
+    qtn_context* x = (qtn_context*)ctx;
+    Ws w;
+    qtn_status st = bind_ws(x, ws, ws_bytes, w);
+    if (st) return st;
+    const int N = psi->n_sites, d = psi->d, cap = psi->chi_cap;
+    const int n = mps_layout_n(psi, layout);
+    const long long total = (long long)llround(pow((double)d, (double)N));
+    if (total > cap_elems) return QTN_ERR_CAPACITY;
+    if (total > w.L.dense) return QTN_ERR_WORKSPACE;
+    cudaStream_t s = x->c.stream;
+    {   // every intermediate d^p x bond[p] must fit the workspace buffers
+        std::vector<int> hb(N + 1);
+        CK(cudaMemcpyAsync(hb.data(), psi->bond, (N + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        long long rows_p = 1;
+        for (int p = 0; p <= N; ++p) {
+            if (hb[p] < 1 || hb[p] > cap) return QTN_ERR_SHAPE;
+            if (rows_p * hb[p] > w.L.dense) return QTN_ERR_CAPACITY;
+            rows_p *= d;
+        }
+        if (hb[0] != 1 || hb[N] != 1) return QTN_ERR_SHAPE;
+    }
+    float2* cur = w.X0;
+    float2* nxt = w.X1;
+    k_set_one<<<1, 1, 0, s>>>(cur);
+    long long rows = 1;
+    for (int p = 0; p < N; ++p) {
+        k_plan_dense<<<1, 1, 0, s>>>(psi->bond, p, d, w.R);
+        GemmDesc g{};
+        g.A = mat(cur, dr(R_TMP0), dc(1));
+        g.B = mat2((const float2*)psi->sites + (size_t)p * cap * d * cap, dc(d * cap), dr(R_TMP1), dc(cap), dc(1));
+        g.C = nxt; g.crs = dr(R_TMP2); g.ccs = dc(1);
+        g.M = dc((int)rows); g.N = dr(R_TMP2); g.K = dr(R_TMP0);
+        g.mode = OUT_STORE; g.alpha_re = 1.f; g.omega_seed = -1;
+        CK(launch_gemm(g, (int)rows, d * cap, cap, w.R, s));
+        std::swap(cur, nxt);
+        rows *= d;
+    }
+    k_quantics_to_dense<<<grid_for(total, 256, x->c.sm_count), 256, 0, s>>>(cur, (float2*)dense, n, layout);
+    CKL();
+    return QTN_OK;
+}
+
+qtn_status qtn_norm2(void* ctx, const qtn_mps* psi, double* norm2, void* ws, size_t ws_bytes) {
+    if (!ctx || !psi || !norm2) return QTN_ERR_ARG;
+    double re_im[2];
+    qtn_status st = qtn_overlap(ctx, psi, psi, re_im, ws, ws_bytes);
+    *norm2 = re_im[0];
+    return st;
+}
+
+qtn_status qtn_overlap(void* ctx, const qtn_mps* a, const qtn_mps* b, double* result, void* ws, size_t ws_bytes) {
+    if (!ctx || !a || !b || !result || a->n_sites != b->n_sites || a->d != b->d) return QTN_ERR_ARG;
+    qtn_context* x = (qtn_context*)ctx;
+    Ws w;
+    qtn_status st = bind_ws(x, ws, ws_bytes, w);
+    if (st) return st;
+    cudaStream_t s = x->c.stream;
+    const int N = a->n_sites, d = a->d;
+    const int gld = std::max(w.L.m_cap, w.L.p_cap);
+    if (a->chi_cap > gld || b->chi_cap > gld) return QTN_ERR_WORKSPACE;
+    std::vector<int> ba(N + 1), bb(N + 1);
+    CK(cudaMemcpyAsync(ba.data(), a->bond, (N + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(bb.data(), b->bond, (N + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double2 one = make_double2(1.0, 0.0);
+    double2* E = w.G64;
+    double2* En = w.S64;
+    CK(cudaMemcpyAsync(E, &one, sizeof(double2), cudaMemcpyHostToDevice, s));
+    for (int p = 0; p < N; ++p) {
+        const float2* A = (const float2*)a->sites + (size_t)p * a->chi_cap * d * a->chi_cap;
+        const float2* B = (const float2*)b->sites + (size_t)p * b->chi_cap * d * b->chi_cap;
+        k_transfer_step<<<ba[p + 1], 128, 0, s>>>(E, gld, A, a->chi_cap, ba[p], ba[p + 1], B, b->chi_cap, bb[p],
+                                                  bb[p + 1], d, En);
+        CKL();
+        std::swap(E, En);
+    }
+    double2 h;
+    CK(cudaMemcpyAsync(&h, E, sizeof(double2), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    result[0] = h.x;
+    result[1] = h.y;
+    return QTN_OK;
+}
+
+qtn_status qtn_amplitudes(void* ctx, const qtn_mps* psi, const int* digits, int count, void* out, void* ws,
+                          size_t ws_bytes) {
+    if (!ctx || !psi || !digits || !out || count < 0) return QTN_ERR_ARG;
+    qtn_context* x = (qtn_context*)ctx;
+    Ws w;
+    qtn_status st = bind_ws(x, ws, ws_bytes, w);
+    if (st) return st;
+    const int cap = psi->chi_cap;
+    const long long per = 2ll * cap;
+    const long long room = w.L.dense > 0 ? w.L.dense : 0;
+    const int batch = (int)std::max(1LL, std::min<long long>(count, room / per));
+    if (room < per) return QTN_ERR_WORKSPACE;
+    for (int s0 = 0; s0 < count; s0 += batch) {
+        const int cnt = std::min(batch, count - s0);
+        const int threads = 256;
+        const int blocks = (cnt * 32 + threads - 1) / threads;
+        k_amplitudes<<<blocks, threads, 0, x->c.stream>>>((const float2*)psi->sites, psi->bond, psi->n_sites, psi->d,
+                                                         cap, digits + (size_t)s0 * psi->n_sites, cnt,
+                                                         (float2*)out + s0, w.X0);
+        CKL();
+    }
+    return QTN_OK;
+}
+
+}  // extern "C"

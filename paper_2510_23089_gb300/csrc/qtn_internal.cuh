@@ -1,0 +1,140 @@
+// Internal declarations of the quantics tensor-network library (sm_103a).
+//
+// Data-dependent sizes (bond dimensions chosen by truncation) never travel to
+// the host in the hot path: they live in a small array of device "dimension
+// registers" in the workspace.  Every kernel receives Dim descriptors that are
+// evaluated on the device (value = R[reg] * mul + add, or a constant), and is
+// launched with a grid sized by capacities, retiring the blocks that fall
+// outside the live extent.  A whole zip-up pass is therefore a fixed sequence
+// of launches that can be captured in a CUDA graph.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/qtn.h"
+
+namespace qtn {
+
+// ------------------------------------------------------------------ complex helpers
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// acc += a * b
+__device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+}
+
+// ------------------------------------------------------------------ dimension registers
+enum Reg : int {
+    R_CHILN = 0,   // left bond of the site being produced (= rows of the carry)
+    R_CHIL,        // left bond of the input site
+    R_CHIR,        // right bond of the input site
+    R_WL,          // MPO left bond at this site (1 for identity sites)
+    R_WR,          // MPO right bond
+    R_M,           // rows of the unfolded matrix T (chiLn * d)
+    R_N,           // columns of T (wR * chiR)
+    R_K,           // rank kept by the truncation
+    R_P,           // subspace size of the randomised range finder
+    R_LAST,        // 1 at the last site of a sweep
+    R_MID,         // helper: chiLn * wL
+    R_DN,          // helper: d * chiR
+    R_ENC_ROWS,    // encode: rows of the current unfolding
+    R_ENC_COLS,    // encode: columns of the current unfolding
+    R_TMP0, R_TMP1, R_TMP2, R_TMP3,
+    R_SWEEPS = 20, // statistics: largest Jacobi sweep count
+    R_FLAGS = 21,  // statistics: bit 0 no convergence, bit 1 capacity clamp, bit 2 non-finite
+    R_MAXBOND = 22,
+    R_COUNT = 32
+};
+
+struct Dim {
+    int c, reg, mul, add;
+    __host__ __device__ __forceinline__ int eval(const int* R) const { return reg >= 0 ? R[reg] * mul + add : c; }
+};
+inline Dim dc(int v) { return Dim{v, -1, 0, 0}; }
+inline Dim dr(int reg, int mul = 1, int add = 0) { return Dim{0, reg, mul, add}; }
+
+// A strided complex matrix view: element (i, j) at
+//   p[i*rs + j*cs]                                   (jdiv unset), or
+//   p[i*rs + (j / jdiv)*cs_hi + (j % jdiv)*cs]       (jdiv set: a column index made of two digits,
+//                                                     e.g. (physical index, bond index) of a padded site)
+// optionally conjugated.
+struct Mat {
+    const float2* p;
+    Dim rs, cs;
+    int conj;
+    Dim jdiv, cs_hi;
+};
+inline Mat mat(const void* p, Dim rs, Dim cs, int conj = 0) {
+    return Mat{(const float2*)p, rs, cs, conj, Dim{0, -1, 0, 0}, Dim{0, -1, 0, 0}};
+}
+inline Mat mat2(const void* p, Dim rs, Dim jdiv, Dim cs_hi, Dim cs, int conj = 0) {
+    return Mat{(const float2*)p, rs, cs, conj, jdiv, cs_hi};
+}
+
+// Output modes of the generic GEMM.
+enum OutMode : int { OUT_STORE = 0, OUT_ACCUM = 1, OUT_ATOMIC64 = 2 };
+
+struct GemmDesc {
+    Mat A, B;          // C(MxN) = alpha * A(MxK) * B(KxN)
+    void* C;           // float2* (STORE/ACCUM) or double2* (ATOMIC64)
+    Dim crs, ccs;      // C strides
+    Dim M, N, K;
+    int mode;
+    int kchunk;        // ATOMIC64: K split into chunks of this size across blockIdx.z
+    float alpha_re, alpha_im;
+    int omega_seed;    // >= 0: B is a generated pseudo-random Gaussian matrix (B.p ignored)
+};
+
+// ------------------------------------------------------------------ ledger (device doubles in the workspace)
+enum Ledger : int {
+    L_DISCARDED = 0,  // accumulated discarded weight of the current call
+    L_NORM2,          // squared norm of the result
+    L_TRACE,          // scratch: total weight of the current factorisation
+    L_FLAGS,          // bit flags (as double, written with atomicOr on an int view)
+    L_SWEEPS,         // max sweeps used
+    L_MAXBOND,
+    L_COUNT = 16
+};
+
+// ------------------------------------------------------------------ workspace layout
+struct WsLayout {
+    size_t ledger, regs, T, P, carry, G64, G32, U, lam, Y, Q, S64, Z, X0, X1, omega, total;
+    int m_cap, n_cap, p_cap, chi, d, w, n_sites;
+    long long dense;
+};
+WsLayout ws_layout(int n_sites, int d, int chi_max, int w_max, long long dense_elems);
+
+// ------------------------------------------------------------------ context
+struct Ctx {
+    cudaStream_t stream;
+    int sm_count;
+    int device;
+};
+
+// Pointers into the caller's workspace.
+struct Ws {
+    double* ledger;
+    int* R;
+    float2 *T, *P, *carry, *G32, *U, *Y, *Q, *Z, *X0, *X1;
+    double2 *G64, *S64;
+    double* lam;
+    WsLayout L;
+};
+
+// Largest eigen/SVD problem solved inside one CTA's shared memory.
+constexpr int EIG_MAX = 160;
+
+// ------------------------------------------------------------------ launches (defined in the .cu files)
+cudaError_t launch_gemm(const GemmDesc& d, int max_m, int max_n, int max_k, const int* R, cudaStream_t s);
+cudaError_t launch_eig(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, double* lam, const int* R,
+                       int r_cap, int max_sweeps, double* ledger, cudaStream_t s);
+
+}  // namespace qtn

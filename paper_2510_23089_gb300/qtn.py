@@ -1,0 +1,326 @@
+"""Python binding of the C ABI in include/qtn.h (argument marshalling only).
+
+Device memory and streams come from PyTorch; every computation runs in
+libqtn.so.  The entry points keep the C names without the ``qtn_`` prefix:
+``encode``, ``apply_mpo``, ``truncate``, ``fresnel_step``, ``to_dense``,
+``build_qft_mpo``, ``build_phase_mpo``, ``mpo_dagger``, ``norm2``,
+``overlap``, ``amplitudes``.
+
+There is no fallback: if the library is missing or no CUDA device is present,
+loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqtn.so")
+
+LAYOUTS = {"serial": 0, "interleaved": 1, "1d": 2}
+PRECISIONS = {"fp32": 0, "plain": 0, "mixed": 1}
+CANON = {0: "none", 1: "left", 2: "right"}
+STATUS = {
+    0: "QTN_OK", 1: "QTN_ERR_ARG", 2: "QTN_ERR_SHAPE", 3: "QTN_ERR_CAPACITY", 4: "QTN_ERR_NOCONV",
+    5: "QTN_ERR_NONFINITE", 6: "QTN_ERR_TIMEOUT", 7: "QTN_ERR_CUDA", 8: "QTN_ERR_BOUNDS", 9: "QTN_ERR_WORKSPACE",
+}
+
+# Every symbol include/qtn.h declares (checked by the CPU test-suite).
+EXPORTS = (
+    "qtn_create", "qtn_destroy", "qtn_set_stream", "qtn_status_string", "qtn_version", "qtn_workspace_size",
+    "qtn_encode", "qtn_build_qft_mpo", "qtn_build_phase_mpo", "qtn_mpo_dagger", "qtn_apply_mpo", "qtn_truncate",
+    "qtn_fresnel_step", "qtn_to_dense", "qtn_norm2", "qtn_overlap", "qtn_amplitudes",
+)
+
+
+class QtnError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+class c_mps(ctypes.Structure):
+    _fields_ = [("n_sites", ctypes.c_int), ("d", ctypes.c_int), ("chi_cap", ctypes.c_int), ("canon", ctypes.c_int),
+                ("bond", ctypes.c_void_p), ("sites", ctypes.c_void_p)]
+
+
+class c_mpo(ctypes.Structure):
+    _fields_ = [("n_sites", ctypes.c_int), ("w_cap", ctypes.c_int), ("w_max", ctypes.c_int),
+                ("bond", ctypes.c_void_p), ("sites", ctypes.c_void_p)]
+
+
+class c_trunc(ctypes.Structure):
+    _fields_ = [("chi_max", ctypes.c_int), ("cutoff", ctypes.c_double), ("prec", ctypes.c_int),
+                ("max_sweeps", ctypes.c_int)]
+
+
+class c_stats(ctypes.Structure):
+    _fields_ = [("discarded", ctypes.c_double), ("norm2", ctypes.c_double), ("max_bond", ctypes.c_int),
+                ("sweeps_used", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libqtn.so and declare its signatures.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: run paper_2510_23089_gb300.build.build() first")
+    lib = ctypes.CDLL(path)
+    P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    LL = ctypes.c_longlong
+    mp, op, tr, st = ctypes.POINTER(c_mps), ctypes.POINTER(c_mpo), c_trunc, ctypes.POINTER(c_stats)
+    sig = {
+        "qtn_create": [ctypes.POINTER(P), P], "qtn_destroy": [P], "qtn_set_stream": [P, P],
+        "qtn_workspace_size": [P, I, I, I, I, LL, ctypes.POINTER(S)],
+        "qtn_encode": [P, P, I, I, tr, mp, st, P, S],
+        "qtn_build_qft_mpo": [P, I, I, D, op, P, S],
+        "qtn_build_phase_mpo": [P, I, D, I, D, op, P, S],
+        "qtn_mpo_dagger": [P, op, op],
+        "qtn_apply_mpo": [P, op, I, mp, tr, st, P, S],
+        "qtn_truncate": [P, mp, tr, st, P, S],
+        "qtn_fresnel_step": [P, mp, I, op, op, op, I, tr, st, P, S],
+        "qtn_to_dense": [P, mp, I, P, LL, P, S],
+        "qtn_norm2": [P, mp, ctypes.POINTER(D), P, S],
+        "qtn_overlap": [P, mp, mp, ctypes.POINTER(D), P, S],
+        "qtn_amplitudes": [P, mp, P, I, P, P, S],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = I
+    lib.qtn_status_string.argtypes = [I]
+    lib.qtn_status_string.restype = ctypes.c_char_p
+    lib.qtn_version.argtypes = []
+    lib.qtn_version.restype = I
+    _lib = lib
+    return lib
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise QtnError(code, where)
+
+
+@dataclass
+class Stats:
+    discarded: float
+    norm2: float
+    max_bond: int
+    sweeps_used: int
+    flags: int
+
+
+def _stats(s: c_stats) -> Stats:
+    return Stats(s.discarded, s.norm2, s.max_bond, s.sweeps_used, s.flags)
+
+
+class MPS:
+    """Device MPS in the padded layout of include/qtn.h (torch-owned memory)."""
+
+    def __init__(self, n_sites: int, d: int, chi_cap: int, device="cuda"):
+        self.sites = torch.zeros((n_sites, chi_cap, d, chi_cap), dtype=torch.complex64, device=device)
+        self.bond = torch.ones(n_sites + 1, dtype=torch.int32, device=device)
+        self.c = c_mps(n_sites, d, chi_cap, 0, self.bond.data_ptr(), self.sites.data_ptr())
+
+    @property
+    def n_sites(self):
+        return self.c.n_sites
+
+    @property
+    def d(self):
+        return self.c.d
+
+    @property
+    def chi_cap(self):
+        return self.c.chi_cap
+
+    @property
+    def canon(self) -> str:
+        return CANON[self.c.canon]
+
+    def bonds(self):
+        return [int(b) for b in self.bond.cpu()]
+
+    def to_numpy_sites(self):
+        """Compact site tensors (bond[p], d, bond[p+1]) as complex128 numpy arrays."""
+        b = self.bonds()
+        S = self.sites.cpu().numpy()
+        return [S[p, :b[p], :, :b[p + 1]].astype("complex128") for p in range(self.n_sites)]
+
+    @classmethod
+    def from_numpy_sites(cls, sites, chi_cap: int, canon: str = "none", device="cuda"):
+        N, d = len(sites), sites[0].shape[1]
+        m = cls(N, d, chi_cap, device)
+        host = torch.zeros((N, chi_cap, d, chi_cap), dtype=torch.complex64)
+        bonds = [1]
+        for p, A in enumerate(sites):
+            a, _, b = A.shape
+            host[p, :a, :, :b] = torch.from_numpy(A.astype("complex64"))
+            bonds.append(b)
+        m.sites.copy_(host)
+        m.bond.copy_(torch.tensor(bonds, dtype=torch.int32))
+        m.c.canon = {"none": 0, "left": 1, "right": 2}[canon]
+        return m
+
+    def clone(self):
+        m = MPS(self.n_sites, self.d, self.chi_cap, self.sites.device)
+        m.sites.copy_(self.sites)
+        m.bond.copy_(self.bond)
+        m.c.canon = self.c.canon
+        return m
+
+
+class MPO:
+    """Device per-axis MPO (n sites, d = 2) in the padded layout of include/qtn.h."""
+
+    def __init__(self, n_sites: int, w_cap: int, device="cuda"):
+        self.sites = torch.zeros((n_sites, w_cap, 2, 2, w_cap), dtype=torch.complex64, device=device)
+        self.bond = torch.ones(n_sites + 1, dtype=torch.int32, device=device)
+        self.c = c_mpo(n_sites, w_cap, 1, self.bond.data_ptr(), self.sites.data_ptr())
+
+    @property
+    def n_sites(self):
+        return self.c.n_sites
+
+    @property
+    def w_max(self):
+        return self.c.w_max
+
+    def bonds(self):
+        return [int(b) for b in self.bond.cpu()]
+
+    def to_numpy_cores(self):
+        b = self.bonds()
+        S = self.sites.cpu().numpy()
+        return [S[p, :b[p], :, :, :b[p + 1]].astype("complex128") for p in range(self.n_sites)]
+
+    @classmethod
+    def from_numpy_cores(cls, cores, w_cap: int, device="cuda"):
+        m = cls(len(cores), w_cap, device)
+        host = torch.zeros((len(cores), w_cap, 2, 2, w_cap), dtype=torch.complex64)
+        bonds = [1]
+        for p, c in enumerate(cores):
+            a, _, _, b = c.shape
+            host[p, :a, :, :, :b] = torch.from_numpy(c.astype("complex64"))
+            bonds.append(b)
+        m.sites.copy_(host)
+        m.bond.copy_(torch.tensor(bonds, dtype=torch.int32))
+        m.c.w_max = max(bonds)
+        return m
+
+
+class Engine:
+    """A library context on the current torch stream plus a workspace sized for
+    states of up to ``n_sites`` sites, dimension ``d``, bonds ``chi`` and MPO
+    bonds ``w``, and dense inputs of ``dense`` entries."""
+
+    def __init__(self, n_sites: int, d: int, chi: int, w: int, dense: int = 0, stream=None):
+        self.lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the qtn library has no CPU path")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        ctx = ctypes.c_void_p()
+        _check(self.lib.qtn_create(ctypes.byref(ctx), ctypes.c_void_p(self.stream.cuda_stream)), "qtn_create")
+        self.ctx = ctx
+        nbytes = ctypes.c_size_t()
+        _check(self.lib.qtn_workspace_size(ctx, n_sites, d, chi, w, dense, ctypes.byref(nbytes)),
+               "qtn_workspace_size")
+        self.ws = torch.empty(int(nbytes.value), dtype=torch.uint8, device="cuda")
+        self.ws_bytes = int(nbytes.value)
+
+    def __del__(self):
+        try:
+            if getattr(self, "ctx", None) is not None:
+                self.lib.qtn_destroy(self.ctx)
+                self.ctx = None
+        except Exception:
+            pass
+
+    def _ws(self):
+        return ctypes.c_void_p(self.ws.data_ptr()), ctypes.c_size_t(self.ws_bytes)
+
+    @staticmethod
+    def trunc(chi_max: int, cutoff: float, prec: str = "fp32", max_sweeps: int = 0) -> c_trunc:
+        return c_trunc(int(chi_max), float(cutoff), PRECISIONS[prec], int(max_sweeps))
+
+    # --------------------------------------------------------------- entry points
+    def encode(self, dense: torch.Tensor, n: int, layout: str, out: MPS, chi_max: int, cutoff: float,
+               prec: str = "fp32", stats: bool = True):
+        assert dense.is_cuda and dense.dtype == torch.complex64 and dense.is_contiguous()
+        st = c_stats()
+        _check(self.lib.qtn_encode(self.ctx, ctypes.c_void_p(dense.data_ptr()), n, LAYOUTS[layout],
+                                   self.trunc(chi_max, cutoff, prec), ctypes.byref(out.c),
+                                   ctypes.byref(st) if stats else None, *self._ws()), "qtn_encode")
+        return _stats(st) if stats else None
+
+    def build_qft_mpo(self, n: int, inverse: bool, cutoff: float, w_cap: int = 16) -> MPO:
+        m = MPO(n, w_cap)
+        _check(self.lib.qtn_build_qft_mpo(self.ctx, n, int(inverse), cutoff, ctypes.byref(m.c), *self._ws()),
+               "qtn_build_qft_mpo")
+        return m
+
+    def build_phase_mpo(self, n: int, c: float, cutoff: float, w_cap: int = 64, bit_reversed: bool = True) -> MPO:
+        m = MPO(n, w_cap)
+        _check(self.lib.qtn_build_phase_mpo(self.ctx, n, float(c), int(bit_reversed), cutoff, ctypes.byref(m.c),
+                                            *self._ws()), "qtn_build_phase_mpo")
+        return m
+
+    def mpo_dagger(self, W: MPO) -> MPO:
+        out = MPO(W.n_sites, W.c.w_cap)
+        _check(self.lib.qtn_mpo_dagger(self.ctx, ctypes.byref(W.c), ctypes.byref(out.c)), "qtn_mpo_dagger")
+        return out
+
+    def apply_mpo(self, W: MPO, axis: int, psi: MPS, chi_max: int, cutoff: float, prec: str = "fp32",
+                  stats: bool = True):
+        st = c_stats()
+        _check(self.lib.qtn_apply_mpo(self.ctx, ctypes.byref(W.c), axis, ctypes.byref(psi.c),
+                                      self.trunc(chi_max, cutoff, prec), ctypes.byref(st) if stats else None,
+                                      *self._ws()), "qtn_apply_mpo")
+        return _stats(st) if stats else None
+
+    def truncate(self, psi: MPS, chi_max: int, cutoff: float, prec: str = "fp32", stats: bool = True):
+        st = c_stats()
+        _check(self.lib.qtn_truncate(self.ctx, ctypes.byref(psi.c), self.trunc(chi_max, cutoff, prec),
+                                     ctypes.byref(st) if stats else None, *self._ws()), "qtn_truncate")
+        return _stats(st) if stats else None
+
+    def fresnel_step(self, psi: MPS, layout: str, Q: MPO, Qd: MPO, D: MPO, n_steps: int, chi_max: int,
+                     cutoff: float, prec: str = "fp32", stats: bool = True):
+        st = c_stats()
+        _check(self.lib.qtn_fresnel_step(self.ctx, ctypes.byref(psi.c), LAYOUTS[layout], ctypes.byref(Q.c),
+                                         ctypes.byref(Qd.c), ctypes.byref(D.c), n_steps,
+                                         self.trunc(chi_max, cutoff, prec), ctypes.byref(st) if stats else None,
+                                         *self._ws()), "qtn_fresnel_step")
+        return _stats(st) if stats else None
+
+    def to_dense(self, psi: MPS, layout: str, n: int) -> torch.Tensor:
+        L = 1 << n
+        out = torch.empty((L,) if layout == "1d" else (L, L), dtype=torch.complex64, device="cuda")
+        _check(self.lib.qtn_to_dense(self.ctx, ctypes.byref(psi.c), LAYOUTS[layout], ctypes.c_void_p(out.data_ptr()),
+                                     out.numel(), *self._ws()), "qtn_to_dense")
+        return out
+
+    def norm2(self, psi: MPS) -> float:
+        v = ctypes.c_double()
+        _check(self.lib.qtn_norm2(self.ctx, ctypes.byref(psi.c), ctypes.byref(v), *self._ws()), "qtn_norm2")
+        return v.value
+
+    def overlap(self, a: MPS, b: MPS) -> complex:
+        v = (ctypes.c_double * 2)()
+        _check(self.lib.qtn_overlap(self.ctx, ctypes.byref(a.c), ctypes.byref(b.c), v, *self._ws()), "qtn_overlap")
+        return complex(v[0], v[1])
+
+    def amplitudes(self, psi: MPS, digits: torch.Tensor) -> torch.Tensor:
+        digits = digits.to(device="cuda", dtype=torch.int32).contiguous()
+        out = torch.empty(digits.shape[0], dtype=torch.complex64, device="cuda")
+        _check(self.lib.qtn_amplitudes(self.ctx, ctypes.byref(psi.c), ctypes.c_void_p(digits.data_ptr()),
+                                       digits.shape[0], ctypes.c_void_p(out.data_ptr()), *self._ws()),
+               "qtn_amplitudes")
+        return out

@@ -1,0 +1,60 @@
+"""CPU checks of the boundary: the library builds for sm_103a, loads, and
+exports every entry point include/qtn.h declares (no compute without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "qtn.h")).read()
+    return sorted(set(re.findall(r"\b(qtn_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2510_23089_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary_calls():
+    names = declared_symbols()
+    for required in ("qtn_encode", "qtn_apply_mpo", "qtn_truncate", "qtn_fresnel_step", "qtn_to_dense"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_binding_lists_every_declared_symbol():
+    from paper_2510_23089_gb300 import qtn
+    assert sorted(qtn.EXPORTS) == declared_symbols()
+
+
+def test_status_strings_without_gpu(libpath):
+    lib = ctypes.CDLL(libpath)
+    lib.qtn_status_string.restype = ctypes.c_char_p
+    assert lib.qtn_status_string(0) == b"ok"
+    assert b"workspace" in lib.qtn_status_string(9)
+
+
+def test_argument_errors_without_gpu(libpath):
+    lib = ctypes.CDLL(libpath)
+    # NULL context / NULL output pointers are rejected before any CUDA call
+    assert lib.qtn_create(None, None) == 1
+    assert lib.qtn_workspace_size(None, 4, 4, 8, 2, 0, None) == 1
+
+
+def test_no_cpu_fallback_in_the_product_path():
+    # the package must not import the oracle, and the binding refuses to run without CUDA
+    pkg = os.path.join(ROOT, "paper_2510_23089_gb300")
+    for f in os.listdir(pkg):
+        if f.endswith(".py"):
+            src = open(os.path.join(pkg, f)).read()
+            assert "import oracle" not in src and "from oracle" not in src, f
