@@ -155,6 +155,20 @@ qtn_status qtn_build_phase_mpo(void* ctx, int n, double c, int bit_reversed, dou
 /* Hermitian conjugate of an MPO: out[a, s', s, b] = conj(in[a, s, s', b]). */
 qtn_status qtn_mpo_dagger(void* ctx, const qtn_mpo* in, qtn_mpo* out);
 
+/* Truncated SVD of one matrix, the factorisation every truncation of the
+ * method performs (Sec. IV, App. A: a Schmidt decomposition per bond).
+ *   T       device complex64, m x n row-major (row stride n); not modified.
+ *   U       device complex64 output, m x k_cap row-major (row stride k_cap):
+ *           the kept left singular vectors, orthonormal columns.
+ *   C       device complex64 output, k_cap x n row-major: C = U^dagger T
+ *           (= diag(s) V^dagger), rows in the same order as U's columns.
+ *   k_out   host int: the rank kept by the rule of qtn_trunc (k <= k_cap).
+ *   stats   optional; discarded = |T|^2 - |C|^2 (FP64).
+ * Sizes: m <= d*chi_max and n <= w_max*chi_max of the workspace sizing call.
+ * The call synchronises the stream (it returns k on the host). */
+qtn_status qtn_tsvd(void* ctx, const void* T, int m, int n, qtn_trunc trunc, void* U, void* C, int k_cap,
+                    int* k_out, qtn_stats* stats, void* ws, size_t ws_bytes);
+
 /* Zip-up MPO x MPS application with SVD truncation (Sec. V, Fig. fig_mpo).
  * The per-axis MPO W acts on axis `axis` (0 = x, 1 = y) of psi:
  *   INTERLEAVED: on the x (high) or y (low) bit of every d = 4 site;
@@ -183,7 +197,10 @@ qtn_status qtn_fresnel_step(void* ctx, qtn_mps* psi, qtn_layout layout, const qt
 /* Contract an MPS to its dense field (inverse quantics map of the layout).
  * dense: device complex64 with room for cap_elems entries; the field has
  * d^N entries, written L x L row-major for SERIAL/INTERLEAVED.
- * QTN_ERR_CAPACITY if d^N > cap_elems. */
+ * The contraction runs left to right through intermediates of d^p * bond[p]
+ * entries, which must fit the workspace's dense_elems (bonds produced by
+ * zip-up may exceed the exact Schmidt rank near the chain ends).
+ * QTN_ERR_CAPACITY if d^N > cap_elems or an intermediate does not fit. */
 qtn_status qtn_to_dense(void* ctx, const qtn_mps* psi, qtn_layout layout, void* dense,
                         long long cap_elems, void* ws, size_t ws_bytes);
 

@@ -6,7 +6,9 @@ box that has the driver.  Usable as ``python -m paper_2510_23089_gb300.build``.
 """
 from __future__ import annotations
 
+import hashlib
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -33,17 +35,21 @@ def sources():
 
 def build(verbose: bool = False, extra_flags=None) -> str:
     nv = nvcc()
-    objdir = os.path.join(HERE, "_build")
+    # objects are keyed by host architecture and by a hash of every input, so a tree copied to another
+    # machine (or edited without touching mtimes) never links stale objects
+    objdir = os.path.join(HERE, "_build", platform.machine())
     os.makedirs(objdir, exist_ok=True)
     extra = list(extra_flags or [])
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
+    headers = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh"))
     headers.append(os.path.join(INCLUDE, "qtn.h"))
-    newest_header = max(os.path.getmtime(h) for h in headers)
+    hdr_digest = hashlib.sha256(b"".join(open(h, "rb").read() for h in headers)).hexdigest()
 
     def compile_one(src):
         obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
-        if (os.path.exists(obj) and os.path.getmtime(obj) >= os.path.getmtime(src)
-                and os.path.getmtime(obj) >= newest_header and not extra):
+        stamp = obj + ".sha"
+        key = hashlib.sha256(open(src, "rb").read() + hdr_digest.encode() +
+                             " ".join([nv, *ARCH, *FLAGS, *extra]).encode()).hexdigest()
+        if os.path.exists(obj) and os.path.exists(stamp) and open(stamp).read() == key:
             return obj
         cmd = [nv, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         if verbose:
@@ -53,6 +59,8 @@ def build(verbose: bool = False, extra_flags=None) -> str:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
         if verbose and r.stderr:
             print(r.stderr, flush=True)
+        with open(stamp, "w") as f:
+            f.write(key)
         return obj
 
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:

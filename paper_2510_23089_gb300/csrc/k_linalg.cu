@@ -45,6 +45,7 @@ __device__ __forceinline__ float2 mat_get(const Mat& m, int i, int j, long long 
 }
 
 __global__ void __launch_bounds__(G_THREADS) k_gemm(GemmDesc d, const int* __restrict__ R) {
+    if (d.guard_reg >= 0 && R[d.guard_reg] != d.guard_val) return;
     const int M = d.M.eval(R), N = d.N.eval(R), K = d.K.eval(R);
     const int m0 = blockIdx.y * GB_M, n0 = blockIdx.x * GB_N;
     if (m0 >= M || n0 >= N) return;
@@ -153,6 +154,7 @@ constexpr int EIG_GL = 8;                       // lanes per column pair
 constexpr int EIG_GROUPS = EIG_THREADS / EIG_GL;
 constexpr int EIG_RS = EIG_MAX + 4;             // padded column stride in shared memory
 constexpr float EIG_TOL = 1.0e-6f;
+constexpr float EIG_NOISE = 1.0e-13f;           // |w_i| |w_j| floor (matrix scaled to unit largest diagonal)
 
 __device__ __forceinline__ void circle_pair(int t, int k, int rr, int& i, int& j) {
     // round-robin tournament (circle method) on rr players, round t in [0, rr-2]
@@ -164,7 +166,8 @@ __device__ __forceinline__ void circle_pair(int t, int k, int rr, int& i, int& j
 __global__ void __launch_bounds__(EIG_THREADS, 1)
 k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restrict__ U, Dim ldud,
              double* __restrict__ lam, const int* __restrict__ Rc, int* __restrict__ Rw, int max_sweeps,
-             double* __restrict__ ledger) {
+             double* __restrict__ ledger, int guard_reg, int guard_val) {
+    if (guard_reg >= 0 && Rc[guard_reg] != guard_val) return;
     extern __shared__ float2 W[];                // column-major, W[j*EIG_RS + i]
     __shared__ double nrm[EIG_MAX];
     __shared__ int rank_of[EIG_MAX];
@@ -172,11 +175,22 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
     const int r = rdim.eval(Rc);
     const long long ld = ldd.eval(Rc), ldu = ldud.eval(Rc);
     if (r <= 0) return;
+    __shared__ double gscale;
     const int tid = threadIdx.x;
+    // Scale by the largest diagonal entry so that squared column norms stay inside the FP32 range
+    // (one-sided Jacobi on a Gram matrix works with fourth powers of the singular values).
+    if (tid < 32) {
+        double mx = 0.0;
+        for (int i = tid; i < r; i += 32) mx = fmax(mx, fabs(G[(long long)i * ld + i].x));
+        for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        if (tid == 0) gscale = (mx > 0.0 && isfinite(mx)) ? mx : 1.0;
+    }
+    __syncthreads();
+    const double inv_scale = 1.0 / gscale;
     for (int e = tid; e < r * r; e += EIG_THREADS) {
-        int i = e / r, j = e % r;                // G row-major; W column j holds G[:, j]
+        int i = e / r, j = e % r;                // G row-major; W column j holds G[:, j] / scale
         double2 g = G[(long long)i * ld + j];
-        W[j * EIG_RS + i] = make_float2((float)g.x, (float)g.y);
+        W[j * EIG_RS + i] = make_float2((float)(g.x * inv_scale), (float)(g.y * inv_scale));
     }
     __syncthreads();
 
@@ -211,7 +225,10 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
                     ci += __shfl_xor_sync(gmask, ci, off);
                 }
                 const float cabs = sqrtf(cr * cr + ci * ci);
-                if (!(cabs > EIG_TOL * sqrtf(a * b)) || !(cabs > 1e-30f)) continue;
+                // Columns of the scaled matrix whose norms are both below the FP32 resolution of G are
+                // round-off: rotating them never converges and they are orthonormalised afterwards.
+                const float ab = sqrtf(a) * sqrtf(b);
+                if (!(cabs > EIG_TOL * ab) || !(cabs > 1e-30f) || !(ab > EIG_NOISE)) continue;
                 const float zeta = (b - a) / (2.f * cabs);
                 const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
                 const float cs = rsqrtf(fmaf(tt, tt, 1.f));
@@ -241,7 +258,7 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (tid % 32 == 0) nrm[j] = sqrt(s);
+        if (tid % 32 == 0) nrm[j] = sqrt(s) * gscale;
     }
     __syncthreads();
     for (int j = tid; j < r; j += EIG_THREADS) {
@@ -255,12 +272,83 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
         lam[rk] = v;
     }
     __syncthreads();
+    // Re-orthonormalise the columns in descending-eigenvalue order (classical Gram-Schmidt, two passes):
+    // directions below the FP32 resolution of G are not orthogonal to working precision after Jacobi, and
+    // the new site must be an isometry.  A column that turns out numerically dependent on the previous
+    // ones is replaced by a pseudo-random vector orthogonalised the same way, so the basis stays complete
+    // and no weight of the factorised matrix is lost.
+    __shared__ int col_of_rank[EIG_MAX];
+    __shared__ float coef_r[EIG_MAX], coef_i[EIG_MAX];
+    __shared__ float red_s[32];
+    __shared__ float nrm_cur;
+    for (int j = tid; j < r; j += EIG_THREADS) col_of_rank[rank_of[j]] = j;
+    __syncthreads();
+    const int warp = tid / 32, wl = tid % 32;
+    auto block_norm = [&](float2* w) {
+        float ss = 0.f;
+        for (int row = tid; row < r; row += EIG_THREADS) ss += w[row].x * w[row].x + w[row].y * w[row].y;
+        for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
+        if (wl == 0) red_s[warp] = ss;
+        __syncthreads();
+        if (tid == 0) {
+            float tot = 0.f;
+            for (int q = 0; q < EIG_THREADS / 32; ++q) tot += red_s[q];
+            nrm_cur = sqrtf(tot);
+        }
+        __syncthreads();
+        return nrm_cur;
+    };
+    auto project_out = [&](float2* w, int t) {
+        for (int q = warp; q < t; q += EIG_THREADS / 32) {
+            const float2* u = W + col_of_rank[q] * EIG_RS;
+            float cr = 0.f, ci = 0.f;
+            for (int row = wl; row < r; row += 32) {
+                float2 a = u[row], b = w[row];
+                cr = fmaf(a.x, b.x, fmaf(a.y, b.y, cr));
+                ci = fmaf(a.x, b.y, fmaf(-a.y, b.x, ci));
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                cr += __shfl_xor_sync(0xffffffffu, cr, off);
+                ci += __shfl_xor_sync(0xffffffffu, ci, off);
+            }
+            if (wl == 0) { coef_r[q] = cr; coef_i[q] = ci; }
+        }
+        __syncthreads();
+        for (int row = tid; row < r; row += EIG_THREADS) {
+            float2 acc = w[row];
+            for (int q = 0; q < t; ++q) {
+                const float2 u = W[col_of_rank[q] * EIG_RS + row];
+                acc.x -= coef_r[q] * u.x - coef_i[q] * u.y;
+                acc.y -= coef_r[q] * u.y + coef_i[q] * u.x;
+            }
+            w[row] = acc;
+        }
+        __syncthreads();
+    };
+    auto scale_col = [&](float2* w, float sc) {
+        for (int row = tid; row < r; row += EIG_THREADS) w[row] = cscale(w[row], sc);
+        __syncthreads();
+    };
+    for (int t = 0; t < r; ++t) {
+        float2* w = W + col_of_rank[t] * EIG_RS;
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            if (attempt == 1) {
+                for (int row = tid; row < r; row += EIG_THREADS) w[row] = gauss2(977 + t, row, t);
+                __syncthreads();
+            }
+            const float n0 = block_norm(w);
+            if (!(n0 > 0.f)) continue;
+            scale_col(w, 1.f / n0);
+            project_out(w, t);
+            project_out(w, t);
+            const float na = block_norm(w);
+            if (na > 1e-4f) { scale_col(w, 1.f / na); break; }
+            if (attempt == 1) scale_col(w, 0.f);
+        }
+    }
     for (int e = tid; e < r * r; e += EIG_THREADS) {
         int j = e / r, row = e % r;
-        double v = nrm[j];
-        float inv = v > 0.0 ? (float)(1.0 / v) : 0.f;
-        float2 x = W[j * EIG_RS + row];
-        U[(long long)rank_of[j] * ldu + row] = make_float2(x.x * inv, x.y * inv);
+        U[(long long)rank_of[j] * ldu + row] = W[j * EIG_RS + row];
     }
     if (tid == 0) {
         atomicMax(&Rw[R_SWEEPS], sweep);
@@ -269,7 +357,7 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
 }
 
 cudaError_t launch_eig(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, double* lam, const int* R,
-                       int r_cap, int max_sweeps, double* ledger, cudaStream_t s) {
+                       int r_cap, int max_sweeps, double* ledger, cudaStream_t s, int guard_reg, int guard_val) {
     (void)r_cap;
     size_t smem = (size_t)EIG_MAX * EIG_RS * sizeof(float2);
     static bool configured = false;
@@ -278,7 +366,8 @@ cudaError_t launch_eig(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, doub
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k_eig_jacobi<<<1, EIG_THREADS, smem, s>>>(G, ld, r, U, ldu, lam, R, (int*)R, max_sweeps, ledger);
+    k_eig_jacobi<<<1, EIG_THREADS, smem, s>>>(G, ld, r, U, ldu, lam, R, (int*)R, max_sweeps, ledger, guard_reg,
+                                               guard_val);
     return cudaGetLastError();
 }
 

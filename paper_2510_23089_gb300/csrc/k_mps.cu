@@ -97,8 +97,9 @@ __global__ void k_stage2(const float2* __restrict__ P, float2* __restrict__ T, c
 // ------------------------------------------------------------------ truncation bookkeeping
 
 // Trace of an FP64 Gram matrix (total weight of the factorised matrix) -> ledger[L_TRACE].
-__global__ void k_trace(const double2* __restrict__ G, int ld, Dim rdim, const int* __restrict__ R,
+__global__ void k_trace(const double2* __restrict__ G, int ld, Dim rdim, int* __restrict__ R,
                         double* __restrict__ ledger) {
+    if (R[R_RAND] != 0) return;
     const int r = rdim.eval(R);
     double s = 0.0;
     for (int i = threadIdx.x; i < r; i += blockDim.x) s += G[(long long)i * ld + i].x;
@@ -110,6 +111,139 @@ __global__ void k_trace(const double2* __restrict__ G, int ld, Dim rdim, const i
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += red[w];
         ledger[L_TRACE] = t;
+    }
+}
+
+// Path of the factorisation of an m-row matrix: the shared-memory eigensolver when m <= EIG_MAX, else the
+// range finder on an EIG_MAX-column sketch.
+__global__ void k_path(Dim mdim, int* __restrict__ R, double* __restrict__ ledger) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int m = mdim.eval(R);
+    ledger[L_TRACE] = 0.0;
+    R[R_RAND] = (m > EIG_MAX) ? 1 : 0;
+    R[R_P] = min(m, EIG_MAX);
+    R[R_ROWS] = min(m, EIG_MAX);
+}
+
+// |T|_F^2 in FP64 accumulated into ledger[L_TRACE] (range-finder path: the total weight of the factorised
+// matrix; L_TRACE is zeroed by k_path).
+__global__ void k_total_weight(const float2* __restrict__ T, Dim ldt, Dim mdim, Dim ndim, const int* __restrict__ R,
+                               double* __restrict__ ledger) {
+    if (R[R_RAND] != 1) return;
+    const int m = mdim.eval(R), n = ndim.eval(R);
+    const long long ld = ldt.eval(R);
+    double s = 0.0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)m * n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const float2 v = T[(e / n) * ld + (e % n)];
+        s += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    __shared__ double red[32];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += red[w];
+        atomicAdd(&ledger[L_TRACE], t);
+    }
+}
+
+// Orthonormalise columns [c0, c0 + CGS_B) of the row-major m x ld matrix Q among themselves with classical
+// Gram-Schmidt applied twice, in shared memory (m <= CGS_MAXM).  A column that is numerically dependent
+// (residual below 1e-5 of its norm) is set to zero.  The columns are assumed already orthogonal to the
+// columns before c0 (projected out by the caller).
+constexpr int CGS_B = 32, CGS_MAXM = 512;
+
+// Column norms of a row-major m x ld matrix (columns [0, ncols)) -> out (FP32 norms).
+__global__ void k_col_norms(const float2* __restrict__ Q, int ld, Dim mdim, Dim ncols, float* __restrict__ out,
+                            const int* __restrict__ R) {
+    if (R[R_RAND] != 1) return;
+    const int m = mdim.eval(R), nc = ncols.eval(R);
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int c = warp; c < nc; c += nwarps) {
+        float s = 0.f;
+        for (int row = lane; row < m; row += 32) {
+            const float2 v = Q[(long long)row * ld + c];
+            s = fmaf(v.x, v.x, fmaf(v.y, v.y, s));
+        }
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) out[c] = sqrtf(s);
+    }
+}
+
+// pre[c]: norm of column c before any projection; a column whose residual falls below 1e-5 of it is
+// numerically dependent on the columns already orthonormalised and is set to zero.
+__global__ void __launch_bounds__(1024) k_cgs_block(float2* __restrict__ Q, int ld, Dim mdim, int c0,
+                                                    const float* __restrict__ pre, const int* __restrict__ R) {
+    if (R[R_RAND] != 1) return;
+    extern __shared__ float2 S[];              // column-major, S[c * CGS_MAXM + row]
+    __shared__ float cr_s[CGS_B], ci_s[CGS_B], red[32];
+    __shared__ float nrm;
+    const int m = mdim.eval(R);
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    for (int e = tid; e < m * CGS_B; e += blockDim.x) {
+        const int row = e / CGS_B, c = e % CGS_B;
+        S[c * CGS_MAXM + row] = Q[(long long)row * ld + c0 + c];
+    }
+    __syncthreads();
+    auto norm_of = [&](const float2* w) {
+        float ss = 0.f;
+        for (int row = tid; row < m; row += blockDim.x) ss += w[row].x * w[row].x + w[row].y * w[row].y;
+        for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
+        if (lane == 0) red[warp] = ss;
+        __syncthreads();
+        if (tid == 0) {
+            float t = 0.f;
+            for (int q = 0; q < (int)blockDim.x / 32; ++q) t += red[q];
+            nrm = sqrtf(t);
+        }
+        __syncthreads();
+        return nrm;
+    };
+    for (int c = 0; c < CGS_B; ++c) {
+        float2* w = S + c * CGS_MAXM;
+        const float nraw = norm_of(w);
+        const float n0 = (nraw > 1e-5f * pre[c0 + c]) ? nraw : 0.f;   // dependent on earlier blocks
+        const float inv0 = n0 > 0.f ? 1.f / n0 : 0.f;
+        for (int row = tid; row < m; row += blockDim.x) w[row] = cscale(w[row], inv0);
+        __syncthreads();
+        for (int pass = 0; pass < 2 && n0 > 0.f; ++pass) {
+            for (int q = warp; q < c; q += blockDim.x / 32) {
+                const float2* u = S + q * CGS_MAXM;
+                float ar = 0.f, ai = 0.f;
+                for (int row = lane; row < m; row += 32) {
+                    const float2 a = u[row], b = w[row];
+                    ar = fmaf(a.x, b.x, fmaf(a.y, b.y, ar));
+                    ai = fmaf(a.x, b.y, fmaf(-a.y, b.x, ai));
+                }
+                for (int off = 16; off > 0; off >>= 1) {
+                    ar += __shfl_xor_sync(0xffffffffu, ar, off);
+                    ai += __shfl_xor_sync(0xffffffffu, ai, off);
+                }
+                if (lane == 0) { cr_s[q] = ar; ci_s[q] = ai; }
+            }
+            __syncthreads();
+            for (int row = tid; row < m; row += blockDim.x) {
+                float2 acc = w[row];
+                for (int q = 0; q < c; ++q) {
+                    const float2 u = S[q * CGS_MAXM + row];
+                    acc.x -= cr_s[q] * u.x - ci_s[q] * u.y;
+                    acc.y -= cr_s[q] * u.y + ci_s[q] * u.x;
+                }
+                w[row] = acc;
+            }
+            __syncthreads();
+        }
+        const float na = norm_of(w);
+        const float sc = (n0 > 0.f && na > 1e-5f) ? 1.f / na : 0.f;
+        for (int row = tid; row < m; row += blockDim.x) w[row] = cscale(w[row], sc);
+        __syncthreads();
+    }
+    for (int e = tid; e < m * CGS_B; e += blockDim.x) {
+        const int row = e / CGS_B, c = e % CGS_B;
+        Q[(long long)row * ld + c0 + c] = S[c * CGS_MAXM + row];
     }
 }
 
@@ -136,7 +270,9 @@ __global__ void k_row_weights(const float2* __restrict__ X, Dim ldx, Dim rows, D
 // weight (total - kept) is <= cutoff * total, cap by chi_max and the capacity.  total = trace of the
 // Gram matrix (the exact weight of the factorised matrix).  Writes perm[0..k), R[R_K], discarded.
 __global__ void k_select(const double* __restrict__ w, Dim rdim, int chi_max, double cutoff, int chi_cap,
-                         int* __restrict__ perm, int* __restrict__ R, double* __restrict__ ledger) {
+                         int total_from_weights, int* __restrict__ perm, int* __restrict__ R,
+                         double* __restrict__ ledger) {
+    if (total_from_weights < 0) total_from_weights = (R[R_RAND] == 0);   // decided on the device
     __shared__ double sorted_w[1024];
     const int r = rdim.eval(R);
     for (int j = threadIdx.x; j < r; j += blockDim.x) {
@@ -151,12 +287,18 @@ __global__ void k_select(const double* __restrict__ w, Dim rdim, int chi_max, do
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const double total = ledger[L_TRACE];
+        // total weight: the sum of all projected weights when the basis spans the whole row space (the same
+        // FP32 projections as the kept weights, so the discarded weight is consistent), else the Gram trace
+        double total = ledger[L_TRACE];
+        if (total_from_weights) {
+            total = 0.0;
+            for (int i = r - 1; i >= 0; --i) total += sorted_w[i];
+        }
         double kept = 0.0;
         int k = 0;
         // directions whose captured weight is below NULL_FLOOR * total are numerically null for FP32 data
-        // (singular value below ~1e-7 of the norm): they are never kept, whatever the cutoff.
-        const double NULL_FLOOR = 1e-14;
+        // (singular value below ~3e-7 of the norm, a few FP32 ulps): they are never kept, whatever the cutoff.
+        const double NULL_FLOOR = 1e-13;
         while (k < r) {
             if (k >= 1 && total - kept <= cutoff * total) break;
             if (k >= 1 && !(sorted_w[k] > NULL_FLOOR * total)) break;
@@ -164,7 +306,9 @@ __global__ void k_select(const double* __restrict__ w, Dim rdim, int chi_max, do
             ++k;
         }
         if (k < 1) k = 1;
-        int kk = min(k, chi_max);
+        // a rank can never exceed the smaller dimension of the factorised matrix
+        const int rank_bound = min(R[R_M], R[R_N]);
+        int kk = min(min(k, chi_max), max(rank_bound, 1));
         if (kk > chi_cap) { kk = chi_cap; R[R_FLAGS] |= 2; }
         kept = 0.0;
         for (int i = 0; i < kk; ++i) kept += sorted_w[i];
@@ -242,6 +386,7 @@ __global__ void k_site_norm2(const float2* __restrict__ site, int cap, int d, co
 // Convert an FP64 matrix to FP32 (r x r, same leading dimension).
 __global__ void k_to_f32(const double2* __restrict__ G, float2* __restrict__ G32, int ld, Dim rdim,
                          const int* __restrict__ R) {
+    if (R[R_RAND] != 1) return;
     const int r = rdim.eval(R);
     const long long total = (long long)r * r;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
@@ -255,6 +400,7 @@ __global__ void k_to_f32(const double2* __restrict__ G, float2* __restrict__ G32
 // Whitening of an eigenbasis: Z[:, j] /= sqrt(lam_j), zeroed below floor * lam_0 (lam sorted descending).
 __global__ void k_whiten(float2* __restrict__ Z, int ldz, const double* __restrict__ lam, Dim rdim, double floor_rel,
                          const int* __restrict__ R) {
+    if (R[R_RAND] != 1) return;
     const int r = rdim.eval(R);
     const double l0 = lam[0];
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * r; e += gridDim.x * blockDim.x) {

@@ -20,9 +20,14 @@ __global__ void k_plan_site(const int*, const int*, int, int, int, int, int, int
 __global__ void k_plan_encode(int, int, int*);
 __global__ void k_reset_stats(int*, double*);
 __global__ void k_stage2(const float2*, float2*, const float2*, int, int, int, int, const int*);
-__global__ void k_trace(const double2*, int, Dim, const int*, double*);
+__global__ void k_trace(const double2*, int, Dim, int*, double*);
+__global__ void k_path(Dim, int*, double*);
+__global__ void k_total_weight(const float2*, Dim, Dim, Dim, const int*, double*);
+__global__ void k_cgs_block(float2*, int, Dim, int, const float*, const int*);
+__global__ void k_col_norms(const float2*, int, Dim, Dim, float*, const int*);
+constexpr int CGS_B = 32, CGS_MAXM = 512;
 __global__ void k_row_weights(const float2*, Dim, Dim, Dim, double*, const int*);
-__global__ void k_select(const double*, Dim, int, double, int, int*, int*, double*);
+__global__ void k_select(const double*, Dim, int, double, int, int, int*, int*, double*);
 __global__ void k_write_site(const float2*, int, const int*, float2*, int, int, int, int*, int, const int*);
 __global__ void k_gather_rows(const float2*, Dim, const int*, float2*, Dim, Dim, const int*);
 __global__ void k_write_last(const float2*, float2*, int, int, int, const int*);
@@ -90,11 +95,11 @@ WsLayout ws_layout(int N, int d, int chi, int w, long long dense) {
     L.P = take((size_t)chi * std::max(w, 1) * d * chi * c8);
     L.carry = take((size_t)chi * nc * c8 + c8);
     L.G64 = take(gdim * gdim * c16);
-    L.G32 = take(gdim * gdim * c8);
+    L.G32 = take(std::max(gdim * gdim, pc * nc) * c8);   // B = Q^dagger T of the range finder
     L.U = take(gdim * gdim * c8);
     L.lam = take(4 * gdim * sizeof(double));
     L.Y = take(gdim * pc * c8);
-    L.Q = take(gdim * pc * c8);
+    L.Q = take(std::max(gdim * pc, pc * pc) * c8);
     L.S64 = take(gdim * gdim * c16);
     L.Z = take(std::max(gdim * nc, pc * pc) * c8);   // projected rows X = U^dagger T (zip-up)
     L.omega = take((size_t)N * chi * d * chi * c8 + (size_t)N * 64 * c8);   // MPS-sized scratch + layer MPO
@@ -173,106 +178,187 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
     cudaStream_t s = c->stream;
     const int mc = io.m_cap;
     const int gld = std::max(w.L.m_cap, w.L.p_cap);
-    CK(cudaMemsetAsync(w.G64, 0, (size_t)mc * gld * sizeof(double2), s));
-    {
+    const int pc = w.L.p_cap;
+    const int max_sweeps = tr.max_sweeps > 0 ? tr.max_sweeps : 30;
+    const int ncap = (int)std::min<long long>(io.n_cap, 1 << 30);
+    k_path<<<1, 1, 0, s>>>(io.m, w.R, w.ledger);
+    CKL();
+    // Gram G = A A^dagger of an m x n matrix with row stride ld (FP32 products, FP64 split-K accumulation)
+    auto gram = [&](const float2* A, Dim m, Dim ld, Dim n, int m_cap, int guard, bool zero,
+                    long long n_cap) -> qtn_status {
+        if (zero) CK(cudaMemsetAsync(w.G64, 0, (size_t)m_cap * gld * sizeof(double2), s));
         GemmDesc g{};
-        g.A = mat(io.T, io.n, dc(1));
-        g.B = mat(io.T, dc(1), io.n, 1);
+        g.A = mat(A, ld, dc(1));
+        g.B = mat(A, dc(1), ld, 1);
         g.C = w.G64; g.crs = dc(gld); g.ccs = dc(1);
-        g.M = io.m; g.N = io.m; g.K = io.n;
+        g.M = m; g.N = m; g.K = n;
         g.mode = OUT_ATOMIC64;
-        int tiles = ((mc + 63) / 64) * ((mc + 63) / 64);
-        long long want = std::max(1, (c->sm_count * 4) / std::max(tiles, 1));
-        long long kc = std::max<long long>(256, (io.n_cap + want - 1) / want);
-        kc = (kc + 15) / 16 * 16;
-        g.kchunk = (int)std::min<long long>(kc, 1 << 30);
-        g.alpha_re = 1.f; g.omega_seed = -1;
-        CK(launch_gemm(g, mc, mc, (int)std::min<long long>(io.n_cap, 1 << 30), w.R, s));
-    }
+        const int tiles = ((m_cap + 63) / 64) * ((m_cap + 63) / 64);
+        const long long want = std::max(1, (c->sm_count * 4) / std::max(tiles, 1));
+        long long kc = std::max<long long>(256, (n_cap + want - 1) / want);
+        g.kchunk = (int)std::min<long long>((kc + 15) / 16 * 16, 1 << 30);
+        if (guard >= 0) { g.guard_reg = R_RAND; g.guard_val = guard; }
+        CK(launch_gemm(g, m_cap, m_cap, (int)std::min<long long>(n_cap, 1 << 30), w.R, s));
+        return QTN_OK;
+    };
+    qtn_status st;
+    // ---- shared-memory path (m <= EIG_MAX): eigenbasis U of G = T T^dagger, X = U^dagger T
+    if ((st = gram(io.T, io.m, io.n, io.n, std::min(mc, EIG_MAX), 0, true, io.n_cap))) return st;
     k_trace<<<1, 256, 0, s>>>(w.G64, gld, io.m, w.R, w.ledger);
     CKL();
-    const int max_sweeps = tr.max_sweeps > 0 ? tr.max_sweeps : 30;
-    Dim rows;
-    if (mc <= EIG_MAX) {
-        CK(launch_eig(w.G64, dc(gld), io.m, w.U, dc(gld), w.lam, w.R, mc, max_sweeps, w.ledger, s));
-        rows = io.m;
-    } else {
-        const int pc = w.L.p_cap;
-        Dim P = dr(R_P);
-        k_to_f32<<<grid_for((long long)mc * mc, 256, c->sm_count), 256, 0, s>>>(w.G64, w.G32, gld, io.m, w.R);
-        CKL();
-        auto gemm_G = [&](const float2* B, int seed) -> qtn_status {   // Y = G32 * B (m x p)
-            GemmDesc g{};
-            g.A = mat(w.G32, dc(gld), dc(1));
-            g.B = mat(B, dc(pc), dc(1));
-            g.C = w.Y; g.crs = dc(pc); g.ccs = dc(1);
-            g.M = io.m; g.N = P; g.K = io.m;
-            g.mode = OUT_STORE; g.alpha_re = 1.f; g.omega_seed = seed;
-            CK(launch_gemm(g, mc, pc, mc, w.R, s));
-            return QTN_OK;
-        };
-        auto gram_p = [&](const float2* A_, const float2* B_) -> qtn_status {   // S64 = A_^dagger B_ (p x p)
-            CK(cudaMemsetAsync(w.S64, 0, (size_t)pc * pc * sizeof(double2), s));
-            GemmDesc g{};
-            g.A = mat(A_, dc(1), dc(pc), 1);
-            g.B = mat(B_, dc(pc), dc(1));
-            g.C = w.S64; g.crs = dc(pc); g.ccs = dc(1);
-            g.M = P; g.N = P; g.K = io.m;
-            g.mode = OUT_ATOMIC64; g.kchunk = 64; g.alpha_re = 1.f; g.omega_seed = -1;
-            CK(launch_gemm(g, pc, pc, mc, w.R, s));
-            return QTN_OK;
-        };
-        auto orth = [&]() -> qtn_status {   // Q = Y (Y^dagger Y)^{-1/2} through the eigenbasis of Y^dagger Y
-            qtn_status st = gram_p(w.Y, w.Y);
-            if (st) return st;
-            CK(launch_eig(w.S64, dc(pc), P, w.Z, dc(pc), ws_lam2(w), w.R, pc, max_sweeps, w.ledger, s));
-            k_whiten<<<grid_for((long long)pc * pc, 256, c->sm_count), 256, 0, s>>>(w.Z, pc, ws_lam2(w), P, 1e-9, w.R);
-            CKL();
-            GemmDesc g{};
-            g.A = mat(w.Y, dc(pc), dc(1));
-            g.B = mat(w.Z, dc(1), dc(pc));
-            g.C = w.Q; g.crs = dc(pc); g.ccs = dc(1);
-            g.M = io.m; g.N = P; g.K = P;
-            g.mode = OUT_STORE; g.alpha_re = 1.f; g.omega_seed = -1;
-            CK(launch_gemm(g, mc, pc, pc, w.R, s));
-            return QTN_OK;
-        };
-        qtn_status st;
-        if ((st = gemm_G(nullptr, 7919))) return st;
-        if ((st = orth())) return st;
-        const int power_iters = 2;
-        for (int it = 0; it < power_iters; ++it) {
-            if ((st = gemm_G(w.Q, -1))) return st;
-            if ((st = orth())) return st;
-        }
-        // Rayleigh-Ritz: H = Q^dagger G Q, eigenbasis Z, Ritz vectors U = Q Z (column-major, ld gld)
-        if ((st = gemm_G(w.Q, -1))) return st;
-        if ((st = gram_p(w.Q, w.Y))) return st;
-        CK(launch_eig(w.S64, dc(pc), P, w.Z, dc(pc), w.lam, w.R, pc, max_sweeps, w.ledger, s));
-        GemmDesc g{};
-        g.A = mat(w.Q, dc(pc), dc(1));
-        g.B = mat(w.Z, dc(1), dc(pc));
-        g.C = w.U; g.crs = dc(1); g.ccs = dc(gld);
-        g.M = io.m; g.N = P; g.K = P;
-        g.mode = OUT_STORE; g.alpha_re = 1.f; g.omega_seed = -1;
-        CK(launch_gemm(g, mc, pc, pc, w.R, s));
-        rows = P;
-    }
-    // X = U^dagger T  (rows x n)
+    CK(launch_eig(w.G64, dc(gld), io.m, w.U, dc(gld), w.lam, w.R, std::min(mc, EIG_MAX), max_sweeps, w.ledger, s,
+                  R_RAND, 0));
     {
         GemmDesc g{};
         g.A = mat(w.U, dc(gld), dc(1), 1);
         g.B = mat(io.T, io.n, dc(1));
         g.C = io.X; g.crs = io.n; g.ccs = dc(1);
-        g.M = rows; g.N = io.n; g.K = io.m;
-        g.mode = OUT_STORE; g.alpha_re = 1.f; g.omega_seed = -1;
-        const int max_rows = (mc <= EIG_MAX) ? mc : w.L.p_cap;
-        CK(launch_gemm(g, max_rows, (int)std::min<long long>(io.n_cap, 1 << 30), mc, w.R, s));
+        g.M = io.m; g.N = io.n; g.K = io.m;
+        g.guard_reg = R_RAND; g.guard_val = 0;
+        CK(launch_gemm(g, std::min(mc, EIG_MAX), ncap, std::min(mc, EIG_MAX), w.R, s));
+    }
+    // ---- range-finder path (m > EIG_MAX): Q = orth(T Omega) by block CGS2, exact path on B = Q^dagger T,
+    //      U = Q U_B.  No product with G is ever formed, so the FP32 dynamic range is that of T itself.
+    if (mc > EIG_MAX) {
+        if (mc > CGS_MAXM) return QTN_ERR_WORKSPACE;
+        const Dim P = dr(R_P);
+        k_total_weight<<<grid_for((long long)mc * ncap, 256, c->sm_count), 256, 0, s>>>(io.T, io.n, io.m, io.n,
+                                                                                            w.R, w.ledger);
+        CKL();
+        float* pre = (float*)ws_lam2(w);                       // pre-projection column norms
+        const long long bcap = (long long)std::max<size_t>((size_t)gld * gld, (size_t)pc * w.L.n_cap);
+        const long long cw = std::max<long long>(1, bcap / pc);  // column chunk of T that fits the B buffer
+        const bool one_chunk = (io.n_cap <= cw);
+        {   // Y = T Omega
+            GemmDesc g{};
+            g.A = mat(io.T, io.n, dc(1));
+            g.C = w.Y; g.crs = dc(pc); g.ccs = dc(1);
+            g.M = io.m; g.N = P; g.K = io.n;
+            g.omega_seed = 7919;
+            g.guard_reg = R_RAND; g.guard_val = 1;
+            CK(launch_gemm(g, mc, pc, ncap, w.R, s));
+        }
+        static bool cgs_configured = false;
+        const size_t cgs_smem = (size_t)CGS_B * CGS_MAXM * sizeof(float2);
+        if (!cgs_configured) {
+            CK(cudaFuncSetAttribute(k_cgs_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cgs_smem));
+            cgs_configured = true;
+        }
+        // orthonormalise the p columns of Yb in place (block classical Gram-Schmidt, twice)
+        auto block_orth = [&](float2* Yb) -> qtn_status {
+            k_col_norms<<<grid_for((long long)pc * 32, 256, c->sm_count), 256, 0, s>>>(Yb, pc, io.m, P, pre, w.R);
+            CKL();
+            for (int b0 = 0; b0 < pc; b0 += CGS_B) {
+                for (int pass = 0; b0 > 0 && pass < 2; ++pass) {   // project out the finished blocks
+                    GemmDesc g{};                                   // Cb = Q[:, :b0]^dagger Y[:, b0:b0+B]
+                    g.A = mat(Yb, dc(1), dc(pc), 1);
+                    g.B = mat(Yb + b0, dc(pc), dc(1));
+                    g.C = w.Z; g.crs = dc(CGS_B); g.ccs = dc(1);
+                    g.M = dc(b0); g.N = dc(CGS_B); g.K = io.m;
+                    g.guard_reg = R_RAND; g.guard_val = 1;
+                    CK(launch_gemm(g, b0, CGS_B, mc, w.R, s));
+                    GemmDesc h{};                                   // Y[:, b0:b0+B] -= Q[:, :b0] Cb
+                    h.A = mat(Yb, dc(pc), dc(1));
+                    h.B = mat(w.Z, dc(CGS_B), dc(1));
+                    h.C = Yb + b0; h.crs = dc(pc); h.ccs = dc(1);
+                    h.M = io.m; h.N = dc(CGS_B); h.K = dc(b0);
+                    h.mode = OUT_ACCUM; h.alpha_re = -1.f;
+                    h.guard_reg = R_RAND; h.guard_val = 1;
+                    CK(launch_gemm(h, mc, CGS_B, b0, w.R, s));
+                }
+                k_cgs_block<<<1, 1024, cgs_smem, s>>>(Yb, pc, io.m, b0, pre, w.R);
+                CKL();
+            }
+            return QTN_OK;
+        };
+        if ((st = block_orth(w.Y))) return st;
+        // one power iteration, Y' = T (T^dagger Q), accumulated over column chunks of T
+        CK(cudaMemsetAsync(w.Q, 0, (size_t)mc * pc * sizeof(float2), s));
+        for (long long c0 = 0; c0 < io.n_cap; c0 += cw) {
+            const int cwid = (int)std::min<long long>(cw, io.n_cap - c0);
+            const Dim ncol = one_chunk ? io.n : dc(cwid);
+            GemmDesc g{};                                           // Z1 = T_c^dagger Q  (cw x p) in the B buffer
+            g.A = mat(io.T + c0, dc(1), io.n, 1);
+            g.B = mat(w.Y, dc(pc), dc(1));
+            g.C = w.G32; g.crs = dc(pc); g.ccs = dc(1);
+            g.M = ncol; g.N = P; g.K = io.m;
+            g.guard_reg = R_RAND; g.guard_val = 1;
+            CK(launch_gemm(g, cwid, pc, mc, w.R, s));
+            GemmDesc h{};                                           // Y' += T_c Z1
+            h.A = mat(io.T + c0, io.n, dc(1));
+            h.B = mat(w.G32, dc(pc), dc(1));
+            h.C = w.Q; h.crs = dc(pc); h.ccs = dc(1);
+            h.M = io.m; h.N = P; h.K = ncol;
+            h.mode = OUT_ACCUM;
+            h.guard_reg = R_RAND; h.guard_val = 1;
+            CK(launch_gemm(h, mc, pc, cwid, w.R, s));
+        }
+        if ((st = block_orth(w.Q))) return st;
+        float2* Qb = w.Q;          // orthonormal basis of the sketch
+        float2* UB = w.Y;          // eigenvectors of the Gram of B (p x p, column-major)
+        // Gram of B = Q^dagger T accumulated over column chunks of T that fit the B buffer (B is never
+        // needed whole: X is formed from T and U directly)
+        CK(cudaMemsetAsync(w.G64, 0, (size_t)pc * gld * sizeof(double2), s));
+        for (long long c0 = 0; c0 < io.n_cap; c0 += cw) {
+            const int cwid = (int)std::min<long long>(cw, io.n_cap - c0);
+            const Dim ncol = one_chunk ? io.n : dc(cwid);
+            GemmDesc g{};
+            g.A = mat(Qb, dc(1), dc(pc), 1);
+            g.B = mat(io.T + c0, io.n, dc(1));
+            g.C = w.G32; g.crs = ncol; g.ccs = dc(1);
+            g.M = P; g.N = ncol; g.K = io.m;
+            g.guard_reg = R_RAND; g.guard_val = 1;
+            CK(launch_gemm(g, pc, cwid, mc, w.R, s));
+            if ((st = gram(w.G32, P, ncol, ncol, pc, 1, false, cwid))) return st;
+        }
+        CK(launch_eig(w.G64, dc(gld), P, UB, dc(pc), w.lam, w.R, pc, max_sweeps, w.ledger, s, R_RAND, 1));
+        {   // U = Q U_B  (m x p, column-major with leading dimension gld)
+            GemmDesc g{};
+            g.A = mat(Qb, dc(pc), dc(1));
+            g.B = mat(UB, dc(1), dc(pc));
+            g.C = w.U; g.crs = dc(1); g.ccs = dc(gld);
+            g.M = io.m; g.N = P; g.K = P;
+            g.guard_reg = R_RAND; g.guard_val = 1;
+            CK(launch_gemm(g, mc, pc, pc, w.R, s));
+        }
+        {   // X = U^dagger T  (p x n)
+            GemmDesc g{};
+            g.A = mat(w.U, dc(gld), dc(1), 1);
+            g.B = mat(io.T, io.n, dc(1));
+            g.C = io.X; g.crs = io.n; g.ccs = dc(1);
+            g.M = P; g.N = io.n; g.K = io.m;
+            g.guard_reg = R_RAND; g.guard_val = 1;
+            CK(launch_gemm(g, pc, ncap, mc, w.R, s));
+        }
+    }
+    const Dim rows = dr(R_ROWS);
+    const int rcap = std::min(mc, EIG_MAX);
+    if (tr.prec == QTN_PLAIN_FP32) {
+        // Refinement: the Gram of the projected rows X = U^dagger T is diagonal up to the FP32 error of the
+        // eigenvectors; a second Jacobi solve on it (a couple of sweeps) gives V2, U <- U V2 and X is formed
+        // again from T.  This removes the ~1e-10 relative weight that first-pass eigenvectors leak into
+        // numerically null directions.
+        if ((st = gram(io.X, rows, io.n, io.n, rcap, -1, true, io.n_cap))) return st;
+        CK(launch_eig(w.G64, dc(gld), rows, w.Y, dc(pc), w.lam, w.R, rcap, max_sweeps, w.ledger, s));
+        GemmDesc g{};                                   // U2 = U V2 (column-major, ld gld) in the Q buffer
+        g.A = mat(w.U, dc(1), dc(gld));
+        g.B = mat(w.Y, dc(1), dc(pc));
+        g.C = w.Q; g.crs = dc(1); g.ccs = dc(gld);
+        g.M = io.m; g.N = rows; g.K = rows;
+        CK(launch_gemm(g, mc, rcap, rcap, w.R, s));
+        GemmDesc h{};                                   // X = U2^dagger T
+        h.A = mat(w.Q, dc(gld), dc(1), 1);
+        h.B = mat(io.T, io.n, dc(1));
+        h.C = io.X; h.crs = io.n; h.ccs = dc(1);
+        h.M = rows; h.N = io.n; h.K = io.m;
+        CK(launch_gemm(h, rcap, ncap, mc, w.R, s));
+        CK(cudaMemcpyAsync(w.U, w.Q, (size_t)gld * rcap * sizeof(float2), cudaMemcpyDeviceToDevice, s));
     }
     k_row_weights<<<grid_for((long long)gld * 32, 256, c->sm_count), 256, 0, s>>>(io.X, io.n, rows, io.n,
                                                                                     ws_weights(w), w.R);
     CKL();
-    k_select<<<1, 256, 0, s>>>(ws_weights(w), rows, tr.chi_max, tr.cutoff, chi_cap_out, ws_perm(w), w.R, w.ledger);
+    k_select<<<1, 256, 0, s>>>(ws_weights(w), rows, tr.chi_max, tr.cutoff, chi_cap_out, -1, ws_perm(w), w.R,
+                               w.ledger);
     CKL();
     rows_out = rows;
     return QTN_OK;
@@ -641,6 +727,49 @@ qtn_status qtn_build_phase_mpo(void* ctx, int n, double c, int bit_reversed, dou
     CK(cudaStreamSynchronize(s));
     out->w_max = *std::max_element(hb.begin(), hb.end());
     return QTN_OK;
+}
+
+__global__ void k_copy_cols(const float2* __restrict__ U, int ldu, const int* __restrict__ perm, float2* __restrict__ out,
+                            int k_cap, int m, const int* __restrict__ R) {
+    const int k = R[R_K];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * k; e += gridDim.x * blockDim.x) {
+        const int i = e / k, j = e % k;
+        out[(long long)i * k_cap + j] = U[(long long)perm[j] * ldu + i];
+    }
+}
+
+qtn_status qtn_tsvd(void* ctx, const void* T, int m, int n, qtn_trunc trunc, void* U, void* C, int k_cap, int* k_out,
+                    qtn_stats* stats, void* ws, size_t ws_bytes) {
+    if (!ctx || !T || !U || !C || !k_out || m < 1 || n < 1 || k_cap < 1) return QTN_ERR_ARG;
+    qtn_context* x = (qtn_context*)ctx;
+    Ws w;
+    qtn_status st = bind_ws(x, ws, ws_bytes, w);
+    if (st) return st;
+    if (m > w.L.m_cap || (long long)m * n > (long long)w.L.m_cap * w.L.n_cap) return QTN_ERR_WORKSPACE;
+    cudaStream_t s = x->c.stream;
+    k_reset_stats<<<1, 1, 0, s>>>(w.R, w.ledger);
+    k_set_reg<<<1, 1, 0, s>>>(w.R, R_M, m);
+    k_set_reg<<<1, 1, 0, s>>>(w.R, R_N, n);
+    k_set_reg<<<1, 1, 0, s>>>(w.R, R_P, std::min(m, EIG_MAX));
+    CKL();
+    qtn_trunc t2 = trunc;
+    if (t2.chi_max <= 0 || t2.chi_max > k_cap) t2.chi_max = k_cap;
+    // the factorised matrix is copied to T-space so that the projection buffer has its capacity layout
+    TsvdIO io{(const float2*)T, dr(R_M), dr(R_N), m, (long long)n, w.Z};
+    Dim rows;
+    st = tsvd(&x->c, w, io, t2, k_cap, rows);
+    if (st) return st;
+    const int gld = std::max(w.L.m_cap, w.L.p_cap);
+    k_copy_cols<<<grid_for((long long)m * k_cap, 256, x->c.sm_count), 256, 0, s>>>(w.U, gld, ws_perm(w), (float2*)U,
+                                                                                   k_cap, m, w.R);
+    k_gather_rows<<<grid_for((long long)k_cap * n, 256, x->c.sm_count), 256, 0, s>>>(w.Z, dr(R_N), ws_perm(w),
+                                                                                      (float2*)C, dr(R_N), dr(R_N), w.R);
+    CKL();
+    int hk = 0;
+    CK(cudaMemcpyAsync(&hk, w.R + R_K, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *k_out = hk;
+    return fill_stats(&x->c, w, stats);
 }
 
 qtn_status qtn_mpo_dagger(void* ctx, const qtn_mpo* in, qtn_mpo* out) {

@@ -51,6 +51,8 @@ enum Reg : int {
     R_SWEEPS = 20, // statistics: largest Jacobi sweep count
     R_FLAGS = 21,  // statistics: bit 0 no convergence, bit 1 capacity clamp, bit 2 non-finite
     R_MAXBOND = 22,
+    R_RAND = 23,   // 1 when the current factorisation takes the range-finder path (m > EIG_MAX)
+    R_ROWS = 24,   // rows of the projected matrix U^dagger T (m, or the subspace size)
     R_COUNT = 32
 };
 
@@ -87,10 +89,12 @@ struct GemmDesc {
     void* C;           // float2* (STORE/ACCUM) or double2* (ATOMIC64)
     Dim crs, ccs;      // C strides
     Dim M, N, K;
-    int mode;
-    int kchunk;        // ATOMIC64: K split into chunks of this size across blockIdx.z
-    float alpha_re, alpha_im;
-    int omega_seed;    // >= 0: B is a generated pseudo-random Gaussian matrix (B.p ignored)
+    int mode = OUT_STORE;
+    int kchunk = 0;        // ATOMIC64: K split into chunks of this size across blockIdx.z
+    float alpha_re = 1.f, alpha_im = 0.f;
+    int omega_seed = -1;   // >= 0: B is a generated pseudo-random Gaussian matrix (B.p ignored)
+    int guard_reg = -1;    // >= 0: the launch does nothing unless R[guard_reg] == guard_val
+    int guard_val = 0;
 };
 
 // ------------------------------------------------------------------ ledger (device doubles in the workspace)
@@ -135,6 +139,6 @@ constexpr int EIG_MAX = 160;
 // ------------------------------------------------------------------ launches (defined in the .cu files)
 cudaError_t launch_gemm(const GemmDesc& d, int max_m, int max_n, int max_k, const int* R, cudaStream_t s);
 cudaError_t launch_eig(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, double* lam, const int* R,
-                       int r_cap, int max_sweeps, double* ledger, cudaStream_t s);
+                       int r_cap, int max_sweeps, double* ledger, cudaStream_t s, int guard_reg = -1, int guard_val = 0);
 
 }  // namespace qtn

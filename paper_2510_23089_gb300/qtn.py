@@ -32,7 +32,7 @@ STATUS = {
 EXPORTS = (
     "qtn_create", "qtn_destroy", "qtn_set_stream", "qtn_status_string", "qtn_version", "qtn_workspace_size",
     "qtn_encode", "qtn_build_qft_mpo", "qtn_build_phase_mpo", "qtn_mpo_dagger", "qtn_apply_mpo", "qtn_truncate",
-    "qtn_fresnel_step", "qtn_to_dense", "qtn_norm2", "qtn_overlap", "qtn_amplitudes",
+    "qtn_fresnel_step", "qtn_to_dense", "qtn_norm2", "qtn_overlap", "qtn_amplitudes", "qtn_tsvd",
 )
 
 
@@ -90,6 +90,7 @@ def load_library(path: str = LIB_PATH):
         "qtn_norm2": [P, mp, ctypes.POINTER(D), P, S],
         "qtn_overlap": [P, mp, mp, ctypes.POINTER(D), P, S],
         "qtn_amplitudes": [P, mp, P, I, P, P, S],
+        "qtn_tsvd": [P, P, I, I, tr, P, P, I, ctypes.POINTER(I), st, P, S],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -316,6 +317,21 @@ class Engine:
         v = (ctypes.c_double * 2)()
         _check(self.lib.qtn_overlap(self.ctx, ctypes.byref(a.c), ctypes.byref(b.c), v, *self._ws()), "qtn_overlap")
         return complex(v[0], v[1])
+
+    def tsvd(self, T: torch.Tensor, chi_max: int, cutoff: float, k_cap: int = None, prec: str = "fp32"):
+        """Truncated SVD of one m x n matrix: returns (U[:, :k], C[:k], stats) with T ~ U C."""
+        assert T.is_cuda and T.dtype == torch.complex64 and T.dim() == 2
+        T = T.contiguous()
+        m, n = T.shape
+        k_cap = k_cap or min(m, n)
+        U = torch.zeros((m, k_cap), dtype=torch.complex64, device="cuda")
+        C = torch.zeros((k_cap, n), dtype=torch.complex64, device="cuda")
+        k = ctypes.c_int()
+        st = c_stats()
+        _check(self.lib.qtn_tsvd(self.ctx, ctypes.c_void_p(T.data_ptr()), m, n, self.trunc(chi_max, cutoff, prec),
+                                 ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(C.data_ptr()), k_cap,
+                                 ctypes.byref(k), ctypes.byref(st), *self._ws()), "qtn_tsvd")
+        return U[:, :k.value], C[:k.value], _stats(st)
 
     def amplitudes(self, psi: MPS, digits: torch.Tensor) -> torch.Tensor:
         digits = digits.to(device="cuda", dtype=torch.int32).contiguous()
