@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark: quantics-MPS Fresnel propagation steps per second.
+
+Workload (default): a 2^16 x 2^16 wavefront (n = 16 interleaved d = 4 sites),
+never densified -- a separable Gaussian beam times a seeded rank-8 smooth phase,
+built on the GPU from per-axis TT-SVD encodings (Kronecker-interleaved, summed,
+compressed to chi = 128).  One step = Q_x, Q_y, D_x, D_y, Q_x^dagger, Q_y^dagger
+applied by zip-up with truncation to chi = 128 (Fig. fig_mpo_mpo of the paper),
+lambda z / dx^2 = 25.3 (lambda = 633 nm, dx = 10 um, z = 4 mm per step).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on the same workload instead.  Multi-GPU runs are independent replicas (the
+path does not shard): value = steps of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Fresnel MPO-MPS steps/s at 2^16², χ=128: mixed vs FP32 plain; % roofline"
+LAMBDA_Z_OVER_DX2 = 25.3
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", choices=["fp32", "mixed"], default="fp32")
+    ap.add_argument("--n", type=int, default=16)
+    ap.add_argument("--chi", type=int, default=128)
+    ap.add_argument("--cutoff", type=float, default=1e-10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-profile", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0
+    import torch
+    import torch.distributed as dist
+    rank, local = int(os.environ["RANK"]), int(os.environ.get("LOCAL_RANK", "0"))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
+    return rank, ws, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"qtn_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- GPU workload
+
+def build_state_gpu(qtn, n: int, chi: int, cutoff: float):
+    """Separable Gaussian beam x rank-8 smooth phase as an interleaved MPS, on the GPU."""
+    import torch
+    import synth
+    fx, gy = synth.separable_phase_factors(n)
+    big = 192                                               # room for one direct sum before compression
+    eng = qtn.Engine(n_sites=n, d=4, chi=big, w=2, dense=1 << n)
+    acc = None
+    for r in range(fx.shape[0]):
+        X = qtn.MPS(n, 2, 32)
+        Y = qtn.MPS(n, 2, 32)
+        eng.encode(torch.from_numpy(fx[r].astype(np.complex64)).cuda(), n, "1d", X, 32, cutoff, stats=False)
+        eng.encode(torch.from_numpy(gy[r].astype(np.complex64)).cuda(), n, "1d", Y, 32, cutoff, stats=False)
+        term = qtn.MPS(n, 4, big)
+        eng.kron_interleave(X, Y, term)
+        if acc is None:
+            acc = term
+        else:
+            s = qtn.MPS(n, 4, big)
+            eng.add(acc, term, s)
+            eng.truncate(s, chi, cutoff, stats=False)
+            acc = s
+    eng.truncate(acc, chi, cutoff, stats=False)
+    out = qtn.MPS(n, 4, chi)
+    out.sites.copy_(acc.sites[:, :chi, :, :chi])
+    out.bond.copy_(acc.bond)
+    out.c.canon = acc.c.canon
+    torch.cuda.synchronize()
+    return out
+
+
+def run_ours(args, rank, ws, local):
+    import torch
+    from paper_2510_23089_gb300 import qtn
+
+    torch.cuda.set_device(local)
+    n, chi = args.n, args.chi
+    L = 1 << n
+    c = LAMBDA_Z_OVER_DX2 / L
+    psi0 = build_state_gpu(qtn, n, chi, args.cutoff)
+    eng = qtn.Engine(n_sites=n, d=4, chi=chi, w=16, dense=0)
+    Q = eng.build_qft_mpo(n, False, 1e-12, w_cap=16)
+    Qd = eng.mpo_dagger(Q)
+    # phase MPO needs a 2^n dense scratch: a separate small engine
+    eng_p = qtn.Engine(n_sites=n, d=2, chi=16, w=2, dense=1 << n)
+    D = eng_p.build_phase_mpo(n, c, 1e-12, w_cap=16)
+    del eng_p
+    psi = psi0.clone()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        eng.fresnel_step(psi, "interleaved", Q, Qd, D, 1, chi, args.cutoff, args.prec, stats=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    profile = not args.no_profile
+    if profile:
+        eng.profile(True)
+    sampler = ClockSampler(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    launches0 = eng.launch_count()
+    sampler.start()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()                                       # evict the L2 between timed steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = eng.launch_count() - launches0
+    barrier(ws)
+    total_ms = max_over_ranks(sum(times), ws)
+    prof = {}
+    if profile:
+        for cls, name in ((0, "k_gemm"), (1, "k_eig_jacobi")):
+            ms, cnt, fl = eng.profile_read(cls)
+            prof[name] = (ms, cnt, fl)
+        eng.profile(False)
+    st = eng.fresnel_step(psi, "interleaved", Q, Qd, D, 0, chi, args.cutoff, args.prec, stats=True)
+
+    # end-to-end through the C ABI with host buffers: pinned host state -> device, one step, result -> host
+    host_sites = psi0.sites.cpu().pin_memory()
+    host_bond = psi0.bond.cpu().pin_memory()
+    out_sites = torch.empty_like(host_sites).pin_memory()
+    out_bond = torch.empty_like(host_bond).pin_memory()
+    e2e_psi = qtn.MPS(n, 4, chi)
+    e2e_t = []
+    for it in range(args.e2e_steps + 1):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e2e_psi.sites.copy_(host_sites, non_blocking=True)
+        e2e_psi.bond.copy_(host_bond, non_blocking=True)
+        e2e_psi.c.canon = psi0.c.canon
+        eng.fresnel_step(e2e_psi, "interleaved", Q, Qd, D, 1, chi, args.cutoff, args.prec, stats=False)
+        out_sites.copy_(e2e_psi.sites, non_blocking=True)
+        out_bond.copy_(e2e_psi.bond, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if it > 0:
+            e2e_t.append(e0.elapsed_time(e1))
+    e2e_ms = max_over_ranks(sum(e2e_t) / max(len(e2e_t), 1), ws)
+    h2d = host_sites.numel() * 8 + host_bond.numel() * 4
+    return {
+        "times": times, "total_ms": total_ms, "clocks": clocks, "launches": launches, "prof": prof,
+        "stats": st, "e2e_ms": e2e_ms, "h2d": h2d, "bonds": psi.bonds(), "Qw": Q.w_max, "Dw": D.w_max,
+    }
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def oracle_state(n: int, chi: int, cutoff: float):
+    import synth
+    from oracle import mps as OS
+    fx, gy = synth.separable_phase_factors(n)
+    acc = None
+    for r in range(fx.shape[0]):
+        X, _ = OS.tt_svd(fx[r], n, 2, 1 << 20, cutoff)
+        Y, _ = OS.tt_svd(gy[r], n, 2, 1 << 20, cutoff)
+        term = OS.kron_interleave(X, Y)
+        acc = term if acc is None else OS.truncate(OS.direct_sum(acc, term), chi, cutoff)[0]
+    return OS.truncate(acc, chi, cutoff)[0]
+
+
+def oracle_step_time(n: int, chi: int, cutoff: float, steps: int):
+    """Seconds per Fresnel step of the FP64 oracle on the same workload (after its own state build)."""
+    from oracle import fresnel as OF
+    from oracle import mpo as OM
+    L = 1 << n
+    c = LAMBDA_Z_OVER_DX2 / L
+    sites = oracle_state(n, chi, cutoff)
+    ops = (OM.qft_mpo_layers(n, 1e-12), None, OM.phase_mpo(n, c, 1e-12))
+    ops = (ops[0], OM.dagger(ops[0]), ops[2])
+    canon = "right"
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sites, canon, _ = OF.fresnel_mps(sites, "interleaved", n, c, chi, cutoff, canon=canon, ops=ops)
+    return (time.perf_counter() - t0) / steps
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        return max((i.get("num_threads", 1) for i in info), default=os.cpu_count())
+    except Exception:
+        return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+# ----------------------------------------------------------------------------- main
+
+def main():
+    args = parse()
+    rank, ws, local = dist_init()
+    config = {"workload": f"quantics interleaved 2^{args.n}x2^{args.n} wavefront, chi={args.chi}, "
+                          "Gaussian beam x rank-8 smooth phase, lambda z/dx^2=25.3 per step",
+              "n_sites": args.n, "d": 4, "chi": args.chi, "cutoff": args.cutoff, "layout": "interleaved",
+              "precision": args.prec, "l2": "flushed between timed steps (state is 8 MB, L2-resident otherwise)"}
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        sec = oracle_step_time(args.n, args.chi, args.cutoff, 1)
+        value = 1.0 / sec
+        line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus, "steps": 1,
+                "warmup": 0, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config, "impl": "reference",
+                "cpu_baseline": {"value": value, "unit": "steps/s", "cores": blas_threads(), "kind": "oracle",
+                                 "sample": "one Fresnel step of the FP64 NumPy oracle on the same workload"},
+                "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    r = run_ours(args, rank, ws, local)
+    steps_all = args.steps * ws
+    value = steps_all / (r["total_ms"] / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["total_ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "fp32" if args.prec == "fp32" else "bf16",
+            "data": "synthetic", "config": config}
+    line["config"]["parallelism"] = f"replicas x{ws}"
+    line["config"]["mpo_bonds"] = {"qft": r["Qw"], "phase": r["Dw"]}
+    line["config"]["state_max_bond"] = max(r["bonds"])
+    line["clocks"] = r["clocks"]
+    line["gpu_launches"] = r["launches"]
+    line["e2e"] = {"value": ws / (r["e2e_ms"] / 1e3), "unit": "steps/s", "h2d_bytes_per_step": r["h2d"],
+                   "d2h_bytes_per_step": r["h2d"]}
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    # FP32 FMA issue rate of the chip: 152 SMs x 128 lanes x 2 FLOP x max SM clock
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    if r["prof"]:
+        dom = max(r["prof"].items(), key=lambda kv: kv[1][0])
+        name, (ms, cnt, fl) = dom
+        achieved = (fl / cnt) / ((ms / cnt) / 1e3) / 1e12 if cnt and ms > 0 else 0.0
+        line["roofline"] = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                            "frac": achieved / alu_peak, "traffic": None,
+                            "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock (derived)",
+                            "launches": cnt, "avg_launch_us": 1e3 * ms / max(cnt, 1),
+                            "share_of_step": ms / r["total_ms"] if r["total_ms"] else None,
+                            "other_classes": {k: {"ms": v[0], "launches": v[1], "flops": v[2]}
+                                              for k, v in r["prof"].items()}}
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        try:
+            sec = oracle_step_time(args.n, args.chi, args.cutoff, 1)
+            line["cpu_baseline"] = {"value": 1.0 / sec, "unit": "steps/s", "cores": blas_threads(), "kind": "oracle",
+                                    "sample": "one Fresnel step of the FP64 NumPy oracle on the same workload "
+                                              "(its own state build excluded)"}
+        except Exception as ex:  # noqa: BLE001
+            line["cpu_baseline"] = {"value": None, "unit": "steps/s", "kind": "oracle", "error": repr(ex)[:200]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

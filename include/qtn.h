@@ -119,6 +119,22 @@ qtn_status qtn_set_stream(void* ctx, void* cuda_stream);
 const char* qtn_status_string(qtn_status s);
 int qtn_version(void);
 
+/* Number of kernels the library has launched in this process (all contexts). */
+long long qtn_launch_count(void);
+
+/* Opt-in kernel profiling (not needed for computation).  While enabled, the
+ * launches of two kernel classes are bracketed by CUDA events on their stream
+ * and their algorithmic FLOPs are accumulated on the device in the workspace:
+ *   class 0: the complex GEMM kernel (8 M N K FLOPs per product);
+ *   class 1: the shared-memory Jacobi eigensolver (16 r FLOPs per evaluated
+ *            column pair, 24 r per rotation, 16 r^3 for the two Gram-Schmidt
+ *            passes).
+ * qtn_profile_read synchronises and returns the total device time (ms), the
+ * launch count and the FLOP total of one class since qtn_profile(.., 1, ..). */
+qtn_status qtn_profile(void* ctx, int enable, void* ws, size_t ws_bytes);
+qtn_status qtn_profile_read(void* ctx, int kernel_class, double* ms, long long* launches, double* flops,
+                            void* ws, size_t ws_bytes);
+
 /* Bytes of device workspace needed by any call on states of n_sites sites of
  * dimension d with bonds up to chi_max, MPOs with bonds up to w_max, and
  * (for qtn_encode) dense inputs of dense_elems complex entries. */
@@ -168,6 +184,20 @@ qtn_status qtn_mpo_dagger(void* ctx, const qtn_mpo* in, qtn_mpo* out);
  * The call synchronises the stream (it returns k on the host). */
 qtn_status qtn_tsvd(void* ctx, const void* T, int m, int n, qtn_trunc trunc, void* U, void* C, int k_cap,
                     int* k_out, qtn_stats* stats, void* ws, size_t ws_bytes);
+
+/* Interleaved d = 4 MPS of the separable field f(x) g(y) from the 1-D MPS
+ * (d = 2, n sites each) of f and g (Sec. III: site p holds mu_p = 2 x_p + y_p,
+ * so each site tensor is the Kronecker product of the two 1-D site tensors and
+ * the bonds multiply).  out: n sites, d = 4, chi_cap >= every product bond
+ * (QTN_ERR_CAPACITY otherwise); must not alias x or y.  Result canon NONE.
+ * The call synchronises (it checks the product bonds on the host). */
+qtn_status qtn_kron_interleave(void* ctx, const qtn_mps* x, const qtn_mps* y, qtn_mps* out);
+
+/* MPS of the sum |a> + |b> (block-diagonal bonds; the boundary sites are
+ * concatenated).  out: same n_sites and d, chi_cap >= bond_a + bond_b at
+ * every inner bond (QTN_ERR_CAPACITY otherwise); must not alias a or b.
+ * Result canon NONE; compress with qtn_truncate.  The call synchronises. */
+qtn_status qtn_add(void* ctx, const qtn_mps* a, const qtn_mps* b, qtn_mps* out);
 
 /* Zip-up MPO x MPS application with SVD truncation (Sec. V, Fig. fig_mpo).
  * The per-axis MPO W acts on axis `axis` (0 = x, 1 = y) of psi:

@@ -11,26 +11,11 @@
 //    round-robin round are processed by 8-lane groups with shuffle reductions.
 //  * k_select: the truncation rule on the sorted spectrum (FP64 bookkeeping).
 #include <math.h>
+#include <stdlib.h>
 
 #include "qtn_internal.cuh"
 
 namespace qtn {
-
-// ------------------------------------------------------------------ pseudo-random Gaussian entries
-__device__ __forceinline__ uint32_t mix32(uint32_t x) {
-    x ^= x >> 16; x *= 0x7feb352dU; x ^= x >> 15; x *= 0x846ca68bU; x ^= x >> 16;
-    return x;
-}
-__device__ __forceinline__ float2 gauss2(int seed, int i, int j) {
-    uint32_t h1 = mix32((uint32_t)i * 0x9E3779B1U ^ mix32((uint32_t)j + 0x85EBCA77U * (uint32_t)(seed + 1)));
-    uint32_t h2 = mix32(h1 ^ 0xC2B2AE3DU);
-    float u1 = ((h1 >> 8) + 1.0f) * (1.0f / 16777217.0f);
-    float u2 = (h2 >> 8) * (1.0f / 16777216.0f);
-    float rad = sqrtf(-2.0f * logf(u1));
-    float s, c;
-    sincospif(2.0f * u2, &s, &c);
-    return make_float2(rad * c, rad * s);
-}
 
 // ------------------------------------------------------------------ GEMM
 constexpr int GB_M = 64, GB_N = 64, GB_K = 16, G_THREADS = 256;
@@ -111,6 +96,8 @@ __global__ void __launch_bounds__(G_THREADS) k_gemm(GemmDesc d, const int* __res
         }
         __syncthreads();
     }
+    if (d.flops != nullptr && threadIdx.x == 0)
+        atomicAdd(d.flops, 8.0 * (double)min(GB_M, M - m0) * (double)min(GB_N, N - n0) * (double)(k_end - k_begin));
     const long long crs = d.crs.eval(R), ccs = d.ccs.eval(R);
     const float2 alpha = make_float2(d.alpha_re, d.alpha_im);
 #pragma unroll
@@ -144,7 +131,11 @@ cudaError_t launch_gemm(const GemmDesc& d, int max_m, int max_n, int max_k, cons
         int kc = d.kchunk > 0 ? d.kchunk : 1;
         grid.z = (unsigned)((max(max_k, 1) + kc - 1) / kc);
     }
-    k_gemm<<<grid, G_THREADS, 0, s>>>(d, R);
+    GemmDesc dd = d;
+    if (g_prof_ledger) dd.flops = g_prof_ledger + L_PROF_GEMM;
+    count_launch(PROF_GEMM, s, true);
+    k_gemm<<<grid, G_THREADS, 0, s>>>(dd, R);
+    count_launch(PROF_GEMM, s, false);
     return cudaGetLastError();
 }
 
@@ -166,7 +157,7 @@ __device__ __forceinline__ void circle_pair(int t, int k, int rr, int& i, int& j
 __global__ void __launch_bounds__(EIG_THREADS, 1)
 k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restrict__ U, Dim ldud,
              double* __restrict__ lam, const int* __restrict__ Rc, int* __restrict__ Rw, int max_sweeps,
-             double* __restrict__ ledger, int guard_reg, int guard_val) {
+             double* __restrict__ ledger, int guard_reg, int guard_val, double* __restrict__ prof, float tol) {
     if (guard_reg >= 0 && Rc[guard_reg] != guard_val) return;
     extern __shared__ float2 W[];                // column-major, W[j*EIG_RS + i]
     __shared__ double nrm[EIG_MAX];
@@ -176,7 +167,9 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
     const long long ld = ldd.eval(Rc), ldu = ldud.eval(Rc);
     if (r <= 0) return;
     __shared__ double gscale;
+    __shared__ unsigned long long n_pairs, n_rot;
     const int tid = threadIdx.x;
+    if (tid == 0) { n_pairs = 0ull; n_rot = 0ull; }
     // Scale by the largest diagonal entry so that squared column norms stay inside the FP32 range
     // (one-sided Jacobi on a Gram matrix works with fourth powers of the singular values).
     if (tid < 32) {
@@ -224,11 +217,12 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
                     cr += __shfl_xor_sync(gmask, cr, off);
                     ci += __shfl_xor_sync(gmask, ci, off);
                 }
+                if (lane == 0 && prof != nullptr) atomicAdd(&n_pairs, 1ull);
                 const float cabs = sqrtf(cr * cr + ci * ci);
                 // Columns of the scaled matrix whose norms are both below the FP32 resolution of G are
                 // round-off: rotating them never converges and they are orthonormalised afterwards.
                 const float ab = sqrtf(a) * sqrtf(b);
-                if (!(cabs > EIG_TOL * ab) || !(cabs > 1e-30f) || !(ab > EIG_NOISE)) continue;
+                if (!(cabs > tol * ab) || !(cabs > 1e-30f) || !(ab > EIG_NOISE)) continue;
                 const float zeta = (b - a) / (2.f * cabs);
                 const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
                 const float cs = rsqrtf(fmaf(tt, tt, 1.f));
@@ -242,7 +236,10 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
                     wi[row] = make_float2(cs * x.x - sn * cey.x, cs * x.y - sn * cey.y);
                     wj[row] = make_float2(sn * ex.x + cs * y.x, sn * ex.y + cs * y.y);
                 }
-                if (lane == 0) rotated = 1;
+                if (lane == 0) {
+                    rotated = 1;
+                    if (prof != nullptr) atomicAdd(&n_rot, 1ull);
+                }
             }
             __syncthreads();
         }
@@ -298,6 +295,8 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
         __syncthreads();
         return nrm_cur;
     };
+    // w -= sum_{q<t} (u_q^dagger w) u_q: coefficients by warps (one dot per warp), then every warp updates a
+    // slice of rows with its lanes splitting the q-sum (all 1024 threads busy).
     auto project_out = [&](float2* w, int t) {
         for (int q = warp; q < t; q += EIG_THREADS / 32) {
             const float2* u = W + col_of_rank[q] * EIG_RS;
@@ -314,14 +313,18 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
             if (wl == 0) { coef_r[q] = cr; coef_i[q] = ci; }
         }
         __syncthreads();
-        for (int row = tid; row < r; row += EIG_THREADS) {
-            float2 acc = w[row];
-            for (int q = 0; q < t; ++q) {
+        for (int row = warp; row < r; row += EIG_THREADS / 32) {
+            float ar = 0.f, ai = 0.f;
+            for (int q = wl; q < t; q += 32) {
                 const float2 u = W[col_of_rank[q] * EIG_RS + row];
-                acc.x -= coef_r[q] * u.x - coef_i[q] * u.y;
-                acc.y -= coef_r[q] * u.y + coef_i[q] * u.x;
+                ar += coef_r[q] * u.x - coef_i[q] * u.y;
+                ai += coef_r[q] * u.y + coef_i[q] * u.x;
             }
-            w[row] = acc;
+            for (int off = 16; off > 0; off >>= 1) {
+                ar += __shfl_xor_sync(0xffffffffu, ar, off);
+                ai += __shfl_xor_sync(0xffffffffu, ai, off);
+            }
+            if (wl == 0) w[row] = make_float2(w[row].x - ar, w[row].y - ai);
         }
         __syncthreads();
     };
@@ -329,6 +332,9 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
         for (int row = tid; row < r; row += EIG_THREADS) w[row] = cscale(w[row], sc);
         __syncthreads();
     };
+    // The Jacobi columns are orthogonal to the solve's tolerance, so one classical pass restores working
+    // precision; a second pass runs when the projection cancelled most of the column ("twice is enough").
+    // A column found dependent gets a pseudo-random replacement.
     for (int t = 0; t < r; ++t) {
         float2* w = W + col_of_rank[t] * EIG_RS;
         for (int attempt = 0; attempt < 2; ++attempt) {
@@ -340,8 +346,11 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
             if (!(n0 > 0.f)) continue;
             scale_col(w, 1.f / n0);
             project_out(w, t);
-            project_out(w, t);
-            const float na = block_norm(w);
+            float na = block_norm(w);
+            if (na < 0.7f) {   // heavy cancellation: a second classical pass restores orthogonality
+                project_out(w, t);
+                na = block_norm(w);
+            }
             if (na > 1e-4f) { scale_col(w, 1.f / na); break; }
             if (attempt == 1) scale_col(w, 0.f);
         }
@@ -353,11 +362,16 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
     if (tid == 0) {
         atomicMax(&Rw[R_SWEEPS], sweep);
         if (!converged) atomicOr(&Rw[R_FLAGS], 1);
+        // algorithmic FLOPs: 16 per row for the three inner products of a pair, 24 per row for a rotation,
+        // 8 r^3 for the classical Gram-Schmidt pass (coefficients and updates, complex)
+        if (prof != nullptr)
+            atomicAdd(prof, 16.0 * r * (double)n_pairs + 24.0 * r * (double)n_rot + 8.0 * (double)r * r * r);
     }
 }
 
 cudaError_t launch_eig(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, double* lam, const int* R,
-                       int r_cap, int max_sweeps, double* ledger, cudaStream_t s, int guard_reg, int guard_val) {
+                       int r_cap, int max_sweeps, double* ledger, cudaStream_t s, int guard_reg, int guard_val,
+                       float tol, int method) {
     (void)r_cap;
     size_t smem = (size_t)EIG_MAX * EIG_RS * sizeof(float2);
     static bool configured = false;
@@ -366,9 +380,76 @@ cudaError_t launch_eig(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, doub
         if (e != cudaSuccess) return e;
         configured = true;
     }
+    // method: 0 = from-scratch solve, 1 = refinement of a nearly diagonal matrix.  Both use one-sided Jacobi
+    // (relative accuracy) unless QTN_EIG=trd selects the Householder-tridiagonal solver for from-scratch
+    // solves (absolute accuracy only; faster on large r).
+    static int use_trd = -1;
+    if (use_trd < 0) {
+        const char* e = getenv("QTN_EIG");
+        use_trd = (e != nullptr && e[0] == 't') ? 1 : 0;
+    }
+    if (method == 0 && use_trd) return launch_eig_trd(G, ld, r, U, ldu, lam, R, s, guard_reg, guard_val);
+    count_launch(PROF_EIG, s, true);
     k_eig_jacobi<<<1, EIG_THREADS, smem, s>>>(G, ld, r, U, ldu, lam, R, (int*)R, max_sweeps, ledger, guard_reg,
-                                               guard_val);
+                                               guard_val, g_prof_ledger ? g_prof_ledger + L_PROF_EIG : nullptr, tol);
+    count_launch(PROF_EIG, s, false);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ launch accounting / profiling
+double* g_prof_ledger = nullptr;
+static long long g_launches = 0;
+static bool g_prof_on = false;
+struct ProfPool {
+    cudaEvent_t* ev = nullptr;   // pairs (start, stop)
+    int cap = 0, used = 0;
+    long long launches = 0;
+};
+static ProfPool g_pool[PROF_NCLASS];
+
+void count_launch(int cls, cudaStream_t s, bool before) {
+    if (!before) ++g_launches;
+    if (!g_prof_on || cls == PROF_OTHER) return;
+    ProfPool& p = g_pool[cls];
+    if (before) {
+        if (p.used + 2 > p.cap) return;
+        cudaEventRecord(p.ev[p.used], s);
+    } else {
+        if (p.used + 2 > p.cap) { ++p.launches; return; }
+        cudaEventRecord(p.ev[p.used + 1], s);
+        p.used += 2;
+        ++p.launches;
+    }
+}
+
+long long launch_total() { return g_launches; }
+
+void prof_begin(bool on, double* ledger) {
+    g_prof_on = on;
+    g_prof_ledger = on ? ledger : nullptr;
+    for (int c = 0; c < PROF_NCLASS; ++c) {
+        ProfPool& p = g_pool[c];
+        if (on && p.ev == nullptr && c != PROF_OTHER) {
+            p.cap = 1 << 16;
+            p.ev = new cudaEvent_t[p.cap];
+            for (int i = 0; i < p.cap; ++i) cudaEventCreate(&p.ev[i]);
+        }
+        p.used = 0;
+        p.launches = 0;
+    }
+}
+
+// Total device time (ms) and launch count of one kernel class since prof_begin.
+void prof_read(int cls, double* ms, long long* launches) {
+    ProfPool& p = g_pool[cls];
+    double t = 0.0;
+    for (int i = 0; i + 1 < p.used; i += 2) {
+        float e = 0.f;
+        cudaEventSynchronize(p.ev[i + 1]);
+        if (cudaEventElapsedTime(&e, p.ev[i], p.ev[i + 1]) == cudaSuccess) t += e;
+    }
+    *ms = t;
+    *launches = p.launches;
 }
 
 }  // namespace qtn

@@ -153,7 +153,6 @@ __global__ void k_total_weight(const float2* __restrict__ T, Dim ldt, Dim mdim, 
 // Gram-Schmidt applied twice, in shared memory (m <= CGS_MAXM).  A column that is numerically dependent
 // (residual below 1e-5 of its norm) is set to zero.  The columns are assumed already orthogonal to the
 // columns before c0 (projected out by the caller).
-constexpr int CGS_B = 32, CGS_MAXM = 512;
 
 // Column norms of a row-major m x ld matrix (columns [0, ncols)) -> out (FP32 norms).
 __global__ void k_col_norms(const float2* __restrict__ Q, int ld, Dim mdim, Dim ncols, float* __restrict__ out,
@@ -175,17 +174,18 @@ __global__ void k_col_norms(const float2* __restrict__ Q, int ld, Dim mdim, Dim 
 
 // pre[c]: norm of column c before any projection; a column whose residual falls below 1e-5 of it is
 // numerically dependent on the columns already orthonormalised and is set to zero.
-__global__ void __launch_bounds__(1024) k_cgs_block(float2* __restrict__ Q, int ld, Dim mdim, int c0,
-                                                    const float* __restrict__ pre, const int* __restrict__ R) {
+template <int NB, int MAXM>
+__device__ __forceinline__ void cgs_block_body(float2* __restrict__ Q, int ld, Dim mdim, int c0,
+                                               const float* __restrict__ pre, const int* __restrict__ R) {
     if (R[R_RAND] != 1) return;
-    extern __shared__ float2 S[];              // column-major, S[c * CGS_MAXM + row]
-    __shared__ float cr_s[CGS_B], ci_s[CGS_B], red[32];
+    extern __shared__ float2 S[];              // column-major, S[c * MAXM + row]
+    __shared__ float cr_s[NB], ci_s[NB], red[32];
     __shared__ float nrm;
     const int m = mdim.eval(R);
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-    for (int e = tid; e < m * CGS_B; e += blockDim.x) {
-        const int row = e / CGS_B, c = e % CGS_B;
-        S[c * CGS_MAXM + row] = Q[(long long)row * ld + c0 + c];
+    for (int e = tid; e < m * NB; e += blockDim.x) {
+        const int row = e / NB, c = e % NB;
+        S[c * MAXM + row] = Q[(long long)row * ld + c0 + c];
     }
     __syncthreads();
     auto norm_of = [&](const float2* w) {
@@ -202,8 +202,8 @@ __global__ void __launch_bounds__(1024) k_cgs_block(float2* __restrict__ Q, int 
         __syncthreads();
         return nrm;
     };
-    for (int c = 0; c < CGS_B; ++c) {
-        float2* w = S + c * CGS_MAXM;
+    for (int c = 0; c < NB; ++c) {
+        float2* w = S + c * MAXM;
         const float nraw = norm_of(w);
         const float n0 = (nraw > 1e-5f * pre[c0 + c]) ? nraw : 0.f;   // dependent on earlier blocks
         const float inv0 = n0 > 0.f ? 1.f / n0 : 0.f;
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(1024) k_cgs_block(float2* __restrict__ Q, int 
         __syncthreads();
         for (int pass = 0; pass < 2 && n0 > 0.f; ++pass) {
             for (int q = warp; q < c; q += blockDim.x / 32) {
-                const float2* u = S + q * CGS_MAXM;
+                const float2* u = S + q * MAXM;
                 float ar = 0.f, ai = 0.f;
                 for (int row = lane; row < m; row += 32) {
                     const float2 a = u[row], b = w[row];
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(1024) k_cgs_block(float2* __restrict__ Q, int 
             for (int row = tid; row < m; row += blockDim.x) {
                 float2 acc = w[row];
                 for (int q = 0; q < c; ++q) {
-                    const float2 u = S[q * CGS_MAXM + row];
+                    const float2 u = S[q * MAXM + row];
                     acc.x -= cr_s[q] * u.x - ci_s[q] * u.y;
                     acc.y -= cr_s[q] * u.y + ci_s[q] * u.x;
                 }
@@ -241,10 +241,19 @@ __global__ void __launch_bounds__(1024) k_cgs_block(float2* __restrict__ Q, int 
         for (int row = tid; row < m; row += blockDim.x) w[row] = cscale(w[row], sc);
         __syncthreads();
     }
-    for (int e = tid; e < m * CGS_B; e += blockDim.x) {
-        const int row = e / CGS_B, c = e % CGS_B;
-        Q[(long long)row * ld + c0 + c] = S[c * CGS_MAXM + row];
+    for (int e = tid; e < m * NB; e += blockDim.x) {
+        const int row = e / NB, c = e % NB;
+        Q[(long long)row * ld + c0 + c] = S[c * MAXM + row];
     }
+}
+
+__global__ void __launch_bounds__(1024) k_cgs_block_32(float2* Q, int ld, Dim mdim, int c0, const float* pre,
+                                                       const int* R) {
+    cgs_block_body<32, 512>(Q, ld, mdim, c0, pre, R);
+}
+__global__ void __launch_bounds__(1024) k_cgs_block_16(float2* Q, int ld, Dim mdim, int c0, const float* pre,
+                                                       const int* R) {
+    cgs_block_body<16, 1024>(Q, ld, mdim, c0, pre, R);
 }
 
 // Squared norms of the rows of X (FP64 accumulation): w[i] = sum_c |X[i, c]|^2.
@@ -613,6 +622,67 @@ __global__ void k_transfer_step(const double2* __restrict__ E, int lde, const fl
             }
         }
         En[(long long)k * lde + l] = make_double2(re, im);
+    }
+}
+
+// ------------------------------------------------------------------ state construction
+
+// Interleaved d = 4 MPS of f(x) g(y) from 1-D MPS of f and g (Sec. III: site p holds mu_p = 2 x_p + y_p):
+// out[(a*by + b), 2s + t, (a'*by' + b')] = X[a, s, a'] Y[b, t, b'].
+__global__ void k_kron_interleave(const float2* __restrict__ X, const int* __restrict__ xb, int xcap,
+                                  const float2* __restrict__ Y, const int* __restrict__ yb, int ycap,
+                                  float2* __restrict__ O, int* __restrict__ ob, int ocap, int n) {
+    const int p = blockIdx.x;
+    if (p >= n) return;
+    const int axl = xb[p], axr = xb[p + 1], byl = yb[p], byr = yb[p + 1];
+    const int ol = axl * byl, orr = axr * byr;
+    const float2* x = X + (long long)p * xcap * 2 * xcap;
+    const float2* y = Y + (long long)p * ycap * 2 * ycap;
+    float2* o = O + (long long)p * ocap * 4 * ocap;
+    for (int e = threadIdx.x; e < ol * 4 * orr; e += blockDim.x) {
+        const int l = e / (4 * orr), mu = (e / orr) % 4, r = e % orr;
+        const int a = l / byl, b = l % byl, a2 = r / byr, b2 = r % byr;
+        const int s = mu >> 1, t = mu & 1;
+        o[((long long)l * 4 + mu) * ocap + r] =
+            cmul(x[((long long)a * 2 + s) * xcap + a2], y[((long long)b * 2 + t) * ycap + b2]);
+    }
+    if (threadIdx.x == 0) {
+        ob[p] = ol;
+        if (p == n - 1) ob[n] = orr;
+    }
+}
+
+// MPS of |A> + |B>: block-diagonal bonds, boundaries concatenated.  O must not alias A or B.
+__global__ void k_direct_sum(const float2* __restrict__ A, const int* __restrict__ ab, int acap,
+                             const float2* __restrict__ B, const int* __restrict__ bb, int bcap,
+                             float2* __restrict__ O, int* __restrict__ ob, int ocap, int N, int d) {
+    const int p = blockIdx.x;
+    if (p >= N) return;
+    const int al = ab[p], ar = ab[p + 1], bl = bb[p], br = bb[p + 1];
+    const int ol = (p == 0) ? 1 : al + bl, orr = (p == N - 1) ? 1 : ar + br;
+    const float2* a = A + (long long)p * acap * d * acap;
+    const float2* b = B + (long long)p * bcap * d * bcap;
+    float2* o = O + (long long)p * ocap * d * ocap;
+    for (int e = threadIdx.x; e < ol * d * orr; e += blockDim.x) {
+        const int l = e / (d * orr), s = (e / orr) % d, r = e % orr;
+        float2 v = make_float2(0.f, 0.f);
+        if (N == 1) {
+            v = cadd(a[s * acap], b[s * bcap]);
+        } else if (p == 0) {
+            if (r < ar) v = a[(long long)s * acap + r];
+            else v = b[(long long)s * bcap + (r - ar)];
+        } else if (p == N - 1) {
+            if (l < al) v = a[((long long)l * d + s) * acap];
+            else v = b[((long long)(l - al) * d + s) * bcap];
+        } else {
+            if (l < al && r < ar) v = a[((long long)l * d + s) * acap + r];
+            else if (l >= al && r >= ar) v = b[((long long)(l - al) * d + s) * bcap + (r - ar)];
+        }
+        o[((long long)l * d + s) * ocap + r] = v;
+    }
+    if (threadIdx.x == 0) {
+        ob[p] = ol;
+        if (p == N - 1) ob[N] = orr;
     }
 }
 

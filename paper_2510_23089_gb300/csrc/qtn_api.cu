@@ -23,9 +23,14 @@ __global__ void k_stage2(const float2*, float2*, const float2*, int, int, int, i
 __global__ void k_trace(const double2*, int, Dim, int*, double*);
 __global__ void k_path(Dim, int*, double*);
 __global__ void k_total_weight(const float2*, Dim, Dim, Dim, const int*, double*);
-__global__ void k_cgs_block(float2*, int, Dim, int, const float*, const int*);
+__global__ void k_cgs_block_32(float2*, int, Dim, int, const float*, const int*);
+__global__ void k_cgs_block_16(float2*, int, Dim, int, const float*, const int*);
 __global__ void k_col_norms(const float2*, int, Dim, Dim, float*, const int*);
-constexpr int CGS_B = 32, CGS_MAXM = 512;
+__global__ void k_kron_interleave(const float2*, const int*, int, const float2*, const int*, int, float2*, int*, int,
+                                  int);
+__global__ void k_direct_sum(const float2*, const int*, int, const float2*, const int*, int, float2*, int*, int, int,
+                             int);
+constexpr int CGS_MAXM_ALL = 1024;
 __global__ void k_row_weights(const float2*, Dim, Dim, Dim, double*, const int*);
 __global__ void k_select(const double*, Dim, int, double, int, int, int*, int*, double*);
 __global__ void k_write_site(const float2*, int, const int*, float2*, int, int, int, int*, int, const int*);
@@ -147,7 +152,15 @@ static float2* ws_mtmp(void* base, const WsLayout& L) { return (float2*)((char*)
             return QTN_ERR_CUDA;                                      \
         }                                                             \
     } while (0)
-#define CKL() CK(cudaGetLastError())
+#define CKL()                           \
+    do {                                \
+        count_launch(PROF_OTHER, 0, false); \
+        CK(cudaGetLastError());         \
+    } while (0)
+
+long long launch_total();
+void prof_begin(bool on, double* ledger);
+void prof_read(int cls, double* ms, long long* launches);
 
 // Relative weight below which a direction of an untruncated (gauge-only) sweep is FP32 round-off.
 constexpr double EXACT_CUTOFF = 1e-13;
@@ -181,6 +194,9 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
     const int pc = w.L.p_cap;
     const int max_sweeps = tr.max_sweeps > 0 ? tr.max_sweeps : 30;
     const int ncap = (int)std::min<long long>(io.n_cap, 1 << 30);
+    // with the FP32 refinement pass the first eigen-solve only has to give a rough basis
+    const bool refine = (tr.prec == QTN_PLAIN_FP32);
+    const float tol1 = refine ? 1e-4f : 1e-6f;
     k_path<<<1, 1, 0, s>>>(io.m, w.R, w.ledger);
     CKL();
     // Gram G = A A^dagger of an m x n matrix with row stride ld (FP32 products, FP64 split-K accumulation)
@@ -207,7 +223,7 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
     k_trace<<<1, 256, 0, s>>>(w.G64, gld, io.m, w.R, w.ledger);
     CKL();
     CK(launch_eig(w.G64, dc(gld), io.m, w.U, dc(gld), w.lam, w.R, std::min(mc, EIG_MAX), max_sweeps, w.ledger, s,
-                  R_RAND, 0));
+                  R_RAND, 0, tol1));
     {
         GemmDesc g{};
         g.A = mat(w.U, dc(gld), dc(1), 1);
@@ -220,7 +236,8 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
     // ---- range-finder path (m > EIG_MAX): Q = orth(T Omega) by block CGS2, exact path on B = Q^dagger T,
     //      U = Q U_B.  No product with G is ever formed, so the FP32 dynamic range is that of T itself.
     if (mc > EIG_MAX) {
-        if (mc > CGS_MAXM) return QTN_ERR_WORKSPACE;
+        if (mc > CGS_MAXM_ALL) return QTN_ERR_WORKSPACE;
+        const int CGS_B = (mc <= 512) ? 32 : 16;
         const Dim P = dr(R_P);
         k_total_weight<<<grid_for((long long)mc * ncap, 256, c->sm_count), 256, 0, s>>>(io.T, io.n, io.m, io.n,
                                                                                             w.R, w.ledger);
@@ -239,9 +256,10 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
             CK(launch_gemm(g, mc, pc, ncap, w.R, s));
         }
         static bool cgs_configured = false;
-        const size_t cgs_smem = (size_t)CGS_B * CGS_MAXM * sizeof(float2);
+        const size_t cgs_smem = (size_t)32 * 512 * sizeof(float2);   // = 16 x 1024 as well
         if (!cgs_configured) {
-            CK(cudaFuncSetAttribute(k_cgs_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cgs_smem));
+            CK(cudaFuncSetAttribute(k_cgs_block_32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cgs_smem));
+            CK(cudaFuncSetAttribute(k_cgs_block_16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cgs_smem));
             cgs_configured = true;
         }
         // orthonormalise the p columns of Yb in place (block classical Gram-Schmidt, twice)
@@ -266,7 +284,8 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
                     h.guard_reg = R_RAND; h.guard_val = 1;
                     CK(launch_gemm(h, mc, CGS_B, b0, w.R, s));
                 }
-                k_cgs_block<<<1, 1024, cgs_smem, s>>>(Yb, pc, io.m, b0, pre, w.R);
+                if (CGS_B == 32) k_cgs_block_32<<<1, 1024, cgs_smem, s>>>(Yb, pc, io.m, b0, pre, w.R);
+                else k_cgs_block_16<<<1, 1024, cgs_smem, s>>>(Yb, pc, io.m, b0, pre, w.R);
                 CKL();
             }
             return QTN_OK;
@@ -311,7 +330,7 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
             CK(launch_gemm(g, pc, cwid, mc, w.R, s));
             if ((st = gram(w.G32, P, ncol, ncol, pc, 1, false, cwid))) return st;
         }
-        CK(launch_eig(w.G64, dc(gld), P, UB, dc(pc), w.lam, w.R, pc, max_sweeps, w.ledger, s, R_RAND, 1));
+        CK(launch_eig(w.G64, dc(gld), P, UB, dc(pc), w.lam, w.R, pc, max_sweeps, w.ledger, s, R_RAND, 1, tol1));
         {   // U = Q U_B  (m x p, column-major with leading dimension gld)
             GemmDesc g{};
             g.A = mat(Qb, dc(pc), dc(1));
@@ -333,13 +352,13 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
     }
     const Dim rows = dr(R_ROWS);
     const int rcap = std::min(mc, EIG_MAX);
-    if (tr.prec == QTN_PLAIN_FP32) {
+    if (refine) {
         // Refinement: the Gram of the projected rows X = U^dagger T is diagonal up to the FP32 error of the
-        // eigenvectors; a second Jacobi solve on it (a couple of sweeps) gives V2, U <- U V2 and X is formed
-        // again from T.  This removes the ~1e-10 relative weight that first-pass eigenvectors leak into
-        // numerically null directions.
+        // first eigenbasis; Jacobi on it converges in a couple of sweeps and, unlike the tridiagonal solver,
+        // keeps every direction accurate relative to its own scale.  U <- U V2 and X is formed again from T.
+        // This removes the weight that first-pass eigenvectors leak into numerically null directions.
         if ((st = gram(io.X, rows, io.n, io.n, rcap, -1, true, io.n_cap))) return st;
-        CK(launch_eig(w.G64, dc(gld), rows, w.Y, dc(pc), w.lam, w.R, rcap, max_sweeps, w.ledger, s));
+        CK(launch_eig(w.G64, dc(gld), rows, w.Y, dc(pc), w.lam, w.R, rcap, max_sweeps, w.ledger, s, -1, 0, 1e-6f, 1));
         GemmDesc g{};                                   // U2 = U V2 (column-major, ld gld) in the Q buffer
         g.A = mat(w.U, dc(1), dc(gld));
         g.B = mat(w.Y, dc(1), dc(pc));
@@ -474,6 +493,37 @@ extern "C" {
 
 int qtn_version(void) { return 1; }
 
+long long qtn_launch_count(void) { return launch_total(); }
+
+qtn_status qtn_profile(void* ctx, int enable, void* ws, size_t ws_bytes) {
+    if (!ctx) return QTN_ERR_ARG;
+    qtn_context* x = (qtn_context*)ctx;
+    double* ledger = nullptr;
+    if (enable) {
+        Ws w;
+        qtn_status st = bind_ws(x, ws, ws_bytes, w);
+        if (st) return st;
+        ledger = w.ledger;
+        CK(cudaMemsetAsync(ledger + L_PROF_GEMM, 0, 2 * sizeof(double), x->c.stream));
+    }
+    prof_begin(enable != 0, ledger);
+    return QTN_OK;
+}
+
+qtn_status qtn_profile_read(void* ctx, int kernel_class, double* ms, long long* launches, double* flops, void* ws,
+                            size_t ws_bytes) {
+    if (!ctx || !ms || !launches || !flops || kernel_class < 0 || kernel_class > 1) return QTN_ERR_ARG;
+    qtn_context* x = (qtn_context*)ctx;
+    Ws w;
+    qtn_status st = bind_ws(x, ws, ws_bytes, w);
+    if (st) return st;
+    CK(cudaStreamSynchronize(x->c.stream));
+    prof_read(kernel_class, ms, launches);
+    CK(cudaMemcpy(flops, w.ledger + (kernel_class == 0 ? L_PROF_GEMM : L_PROF_EIG), sizeof(double),
+                  cudaMemcpyDeviceToHost));
+    return QTN_OK;
+}
+
 const char* qtn_status_string(qtn_status s) {
     switch (s) {
         case QTN_OK: return "ok";
@@ -542,7 +592,9 @@ qtn_status qtn_encode(void* ctx, const void* dense, int n, qtn_layout layout, qt
     Ctx* c = &x->c;
     cudaStream_t s = c->stream;
     k_reset_stats<<<1, 1, 0, s>>>(w.R, w.ledger);
+    CKL();
     k_set_boundary<<<1, 1, 0, s>>>(out->bond, N);
+    CKL();
     k_dense_to_quantics<<<grid_for(total, 256, c->sm_count), 256, 0, s>>>((const float2*)dense, w.X0, n, layout);
     CKL();
     qtn_trunc t2 = trunc;
@@ -554,6 +606,7 @@ qtn_status qtn_encode(void* ctx, const void* dense, int n, qtn_layout layout, qt
     long long ncols = total / d;
     for (int p = 0; p < N - 1; ++p) {
         k_plan_encode<<<1, 1, 0, s>>>(p, d, w.R);
+        CKL();
         k_set_reg<<<1, 1, 0, s>>>(w.R, R_N, (int)ncols);
         CKL();
         TsvdIO io{cur, dr(R_M), dr(R_N), d * cap, ncols, nxt};
@@ -563,13 +616,16 @@ qtn_status qtn_encode(void* ctx, const void* dense, int n, qtn_layout layout, qt
         const int gld = std::max(w.L.m_cap, w.L.p_cap);
         k_write_site<<<grid_for((long long)cap * d * cap, 256, c->sm_count), 256, 0, s>>>(
             w.U, gld, ws_perm(w), (float2*)out->sites + (size_t)p * sstride, cap, d, 0, out->bond, p + 1, w.R);
+        CKL();
         k_gather_rows<<<grid_for((long long)cap * ncols, 256, c->sm_count), 256, 0, s>>>(nxt, dr(R_N), ws_perm(w),
                                                                                           cur, dr(R_N), dr(R_N), w.R);
         CKL();
         ncols /= d;
     }
     k_plan_encode<<<1, 1, 0, s>>>(N - 1, d, w.R);
+    CKL();
     k_write_last<<<1, 256, 0, s>>>(cur, (float2*)out->sites + (size_t)(N - 1) * sstride, cap, d, 0, w.R);
+    CKL();
     k_site_norm2<<<1, 512, 0, s>>>((float2*)out->sites + (size_t)(N - 1) * sstride, cap, d, out->bond, N - 1, w.ledger,
                                    L_NORM2);
     CKL();
@@ -615,6 +671,7 @@ qtn_status qtn_apply_mpo(void* ctx, const qtn_mpo* W, int axis, qtn_mps* psi, qt
     qtn_status st = bind_ws(x, ws, ws_bytes, w);
     if (st) return st;
     k_reset_stats<<<1, 1, 0, x->c.stream>>>(w.R, w.ledger);
+    CKL();
     st = apply_inner(x, w, W, axis, psi, trunc);
     if (st) return st;
     return fill_stats(&x->c, w, stats);
@@ -627,6 +684,7 @@ qtn_status qtn_truncate(void* ctx, qtn_mps* psi, qtn_trunc trunc, qtn_stats* sta
     qtn_status st = bind_ws(x, ws, ws_bytes, w);
     if (st) return st;
     k_reset_stats<<<1, 1, 0, x->c.stream>>>(w.R, w.ledger);
+    CKL();
     if (psi->canon != QTN_CANON_LEFT) {
         qtn_trunc exact = trunc;
         exact.chi_max = psi->chi_cap;
@@ -650,6 +708,7 @@ qtn_status qtn_fresnel_step(void* ctx, qtn_mps* psi, qtn_layout layout, const qt
     qtn_status st = bind_ws(x, ws, ws_bytes, w);
     if (st) return st;
     k_reset_stats<<<1, 1, 0, x->c.stream>>>(w.R, w.ledger);
+    CKL();
     const int naxes = (layout == QTN_LAYOUT_1D) ? 1 : 2;
     const qtn_mpo* ops[3] = {qft, phase, qft_dagger};
     for (int step = 0; step < n_steps; ++step)
@@ -678,6 +737,7 @@ qtn_status qtn_build_qft_mpo(void* ctx, int n, int inverse, double cutoff, qtn_m
     int* laybond = tb + 64;
     qtn_mps stt{n, 4, cap, QTN_CANON_LEFT, inverse ? tb : out->bond, inverse ? (void*)mt : out->sites};
     k_reset_stats<<<1, 1, 0, s>>>(w.R, w.ledger);
+    CKL();
     k_identity_mpo_state<<<n, 32, 0, s>>>((float2*)stt.sites, stt.bond, n, cap);
     CKL();
     qtn_trunc tr{cap, cutoff, QTN_PLAIN_FP32, 0};
@@ -748,8 +808,11 @@ qtn_status qtn_tsvd(void* ctx, const void* T, int m, int n, qtn_trunc trunc, voi
     if (m > w.L.m_cap || (long long)m * n > (long long)w.L.m_cap * w.L.n_cap) return QTN_ERR_WORKSPACE;
     cudaStream_t s = x->c.stream;
     k_reset_stats<<<1, 1, 0, s>>>(w.R, w.ledger);
+    CKL();
     k_set_reg<<<1, 1, 0, s>>>(w.R, R_M, m);
+    CKL();
     k_set_reg<<<1, 1, 0, s>>>(w.R, R_N, n);
+    CKL();
     k_set_reg<<<1, 1, 0, s>>>(w.R, R_P, std::min(m, EIG_MAX));
     CKL();
     qtn_trunc t2 = trunc;
@@ -762,6 +825,7 @@ qtn_status qtn_tsvd(void* ctx, const void* T, int m, int n, qtn_trunc trunc, voi
     const int gld = std::max(w.L.m_cap, w.L.p_cap);
     k_copy_cols<<<grid_for((long long)m * k_cap, 256, x->c.sm_count), 256, 0, s>>>(w.U, gld, ws_perm(w), (float2*)U,
                                                                                    k_cap, m, w.R);
+    CKL();
     k_gather_rows<<<grid_for((long long)k_cap * n, 256, x->c.sm_count), 256, 0, s>>>(w.Z, dr(R_N), ws_perm(w),
                                                                                       (float2*)C, dr(R_N), dr(R_N), w.R);
     CKL();
@@ -770,6 +834,44 @@ qtn_status qtn_tsvd(void* ctx, const void* T, int m, int n, qtn_trunc trunc, voi
     CK(cudaStreamSynchronize(s));
     *k_out = hk;
     return fill_stats(&x->c, w, stats);
+}
+
+qtn_status qtn_kron_interleave(void* ctx, const qtn_mps* x, const qtn_mps* y, qtn_mps* out) {
+    if (!ctx || !x || !y || !out) return QTN_ERR_ARG;
+    const int n = x->n_sites;
+    if (y->n_sites != n || out->n_sites != n || x->d != 2 || y->d != 2 || out->d != 4) return QTN_ERR_SHAPE;
+    if (out->sites == x->sites || out->sites == y->sites) return QTN_ERR_ARG;
+    qtn_context* c = (qtn_context*)ctx;
+    std::vector<int> hx(n + 1), hy(n + 1);
+    CK(cudaMemcpyAsync(hx.data(), x->bond, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost, c->c.stream));
+    CK(cudaMemcpyAsync(hy.data(), y->bond, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost, c->c.stream));
+    CK(cudaStreamSynchronize(c->c.stream));
+    for (int p = 0; p <= n; ++p)
+        if (hx[p] * hy[p] > out->chi_cap) return QTN_ERR_CAPACITY;
+    k_kron_interleave<<<n, 256, 0, c->c.stream>>>((const float2*)x->sites, x->bond, x->chi_cap, (const float2*)y->sites,
+                                                  y->bond, y->chi_cap, (float2*)out->sites, out->bond, out->chi_cap, n);
+    CKL();
+    out->canon = QTN_CANON_NONE;
+    return QTN_OK;
+}
+
+qtn_status qtn_add(void* ctx, const qtn_mps* a, const qtn_mps* b, qtn_mps* out) {
+    if (!ctx || !a || !b || !out) return QTN_ERR_ARG;
+    const int N = a->n_sites, d = a->d;
+    if (b->n_sites != N || out->n_sites != N || b->d != d || out->d != d) return QTN_ERR_SHAPE;
+    if (out->sites == a->sites || out->sites == b->sites) return QTN_ERR_ARG;
+    qtn_context* c = (qtn_context*)ctx;
+    std::vector<int> ha(N + 1), hb(N + 1);
+    CK(cudaMemcpyAsync(ha.data(), a->bond, (N + 1) * sizeof(int), cudaMemcpyDeviceToHost, c->c.stream));
+    CK(cudaMemcpyAsync(hb.data(), b->bond, (N + 1) * sizeof(int), cudaMemcpyDeviceToHost, c->c.stream));
+    CK(cudaStreamSynchronize(c->c.stream));
+    for (int p = 1; p < N; ++p)
+        if (ha[p] + hb[p] > out->chi_cap) return QTN_ERR_CAPACITY;
+    k_direct_sum<<<N, 256, 0, c->c.stream>>>((const float2*)a->sites, a->bond, a->chi_cap, (const float2*)b->sites,
+                                             b->bond, b->chi_cap, (float2*)out->sites, out->bond, out->chi_cap, N, d);
+    CKL();
+    out->canon = QTN_CANON_NONE;
+    return QTN_OK;
 }
 
 qtn_status qtn_mpo_dagger(void* ctx, const qtn_mpo* in, qtn_mpo* out) {
@@ -811,9 +913,11 @@ qtn_status qtn_to_dense(void* ctx, const qtn_mps* psi, qtn_layout layout, void* 
     float2* cur = w.X0;
     float2* nxt = w.X1;
     k_set_one<<<1, 1, 0, s>>>(cur);
+    CKL();
     long long rows = 1;
     for (int p = 0; p < N; ++p) {
         k_plan_dense<<<1, 1, 0, s>>>(psi->bond, p, d, w.R);
+        CKL();
         GemmDesc g{};
         g.A = mat(cur, dr(R_TMP0), dc(1));
         g.B = mat2((const float2*)psi->sites + (size_t)p * cap * d * cap, dc(d * cap), dr(R_TMP1), dc(cap), dc(1));

@@ -31,6 +31,23 @@ __device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
     acc.y = fmaf(a.y, b.x, acc.y);
 }
 
+// ------------------------------------------------------------------ pseudo-random Gaussian entries
+// (deterministic counter-based hash; used for sketch matrices and basis completion, never for results)
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16; x *= 0x7feb352dU; x ^= x >> 15; x *= 0x846ca68bU; x ^= x >> 16;
+    return x;
+}
+__device__ __forceinline__ float2 gauss2(int seed, int i, int j) {
+    uint32_t h1 = mix32((uint32_t)i * 0x9E3779B1U ^ mix32((uint32_t)j + 0x85EBCA77U * (uint32_t)(seed + 1)));
+    uint32_t h2 = mix32(h1 ^ 0xC2B2AE3DU);
+    float u1 = ((h1 >> 8) + 1.0f) * (1.0f / 16777217.0f);
+    float u2 = (h2 >> 8) * (1.0f / 16777216.0f);
+    float rad = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    return make_float2(rad * c, rad * s);
+}
+
 // ------------------------------------------------------------------ dimension registers
 enum Reg : int {
     R_CHILN = 0,   // left bond of the site being produced (= rows of the carry)
@@ -95,6 +112,7 @@ struct GemmDesc {
     int omega_seed = -1;   // >= 0: B is a generated pseudo-random Gaussian matrix (B.p ignored)
     int guard_reg = -1;    // >= 0: the launch does nothing unless R[guard_reg] == guard_val
     int guard_val = 0;
+    double* flops = nullptr;   // profiling: add 8 M N K (this launch's share) here
 };
 
 // ------------------------------------------------------------------ ledger (device doubles in the workspace)
@@ -105,8 +123,15 @@ enum Ledger : int {
     L_FLAGS,          // bit flags (as double, written with atomicOr on an int view)
     L_SWEEPS,         // max sweeps used
     L_MAXBOND,
+    L_PROF_GEMM = 8,  // profiling: algorithmic FLOPs of GEMM launches (8 M N K per complex GEMM)
+    L_PROF_EIG = 9,   // profiling: algorithmic FLOPs of the shared-memory eigensolver
     L_COUNT = 16
 };
+
+// ------------------------------------------------------------------ launch accounting and profiling
+enum ProfClass : int { PROF_GEMM = 0, PROF_EIG = 1, PROF_OTHER = 2, PROF_NCLASS = 3 };
+void count_launch(int cls, cudaStream_t s, bool before);   // brackets a launch with events when profiling
+extern double* g_prof_ledger;                              // ledger receiving device FLOP counts (or null)
 
 // ------------------------------------------------------------------ workspace layout
 struct WsLayout {
@@ -138,7 +163,11 @@ constexpr int EIG_MAX = 160;
 
 // ------------------------------------------------------------------ launches (defined in the .cu files)
 cudaError_t launch_gemm(const GemmDesc& d, int max_m, int max_n, int max_k, const int* R, cudaStream_t s);
+cudaError_t launch_eig_trd(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, double* lam, const int* R,
+                           cudaStream_t s, int guard_reg, int guard_val);
+cudaError_t launch_refine_basis(const double2* G, Dim ld, Dim r, float2* V, int ldv, const int* R, cudaStream_t s);
 cudaError_t launch_eig(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, double* lam, const int* R,
-                       int r_cap, int max_sweeps, double* ledger, cudaStream_t s, int guard_reg = -1, int guard_val = 0);
+                       int r_cap, int max_sweeps, double* ledger, cudaStream_t s, int guard_reg = -1, int guard_val = 0,
+                       float tol = 1e-6f, int method = 0);
 
 }  // namespace qtn

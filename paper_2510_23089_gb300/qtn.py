@@ -33,6 +33,7 @@ EXPORTS = (
     "qtn_create", "qtn_destroy", "qtn_set_stream", "qtn_status_string", "qtn_version", "qtn_workspace_size",
     "qtn_encode", "qtn_build_qft_mpo", "qtn_build_phase_mpo", "qtn_mpo_dagger", "qtn_apply_mpo", "qtn_truncate",
     "qtn_fresnel_step", "qtn_to_dense", "qtn_norm2", "qtn_overlap", "qtn_amplitudes", "qtn_tsvd",
+    "qtn_kron_interleave", "qtn_add", "qtn_launch_count", "qtn_profile", "qtn_profile_read",
 )
 
 
@@ -91,6 +92,10 @@ def load_library(path: str = LIB_PATH):
         "qtn_overlap": [P, mp, mp, ctypes.POINTER(D), P, S],
         "qtn_amplitudes": [P, mp, P, I, P, P, S],
         "qtn_tsvd": [P, P, I, I, tr, P, P, I, ctypes.POINTER(I), st, P, S],
+        "qtn_kron_interleave": [P, mp, mp, mp],
+        "qtn_add": [P, mp, mp, mp],
+        "qtn_profile": [P, I, P, S],
+        "qtn_profile_read": [P, I, ctypes.POINTER(D), ctypes.POINTER(LL), ctypes.POINTER(D), P, S],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -100,6 +105,8 @@ def load_library(path: str = LIB_PATH):
     lib.qtn_status_string.restype = ctypes.c_char_p
     lib.qtn_version.argtypes = []
     lib.qtn_version.restype = I
+    lib.qtn_launch_count.argtypes = []
+    lib.qtn_launch_count.restype = LL
     _lib = lib
     return lib
 
@@ -332,6 +339,28 @@ class Engine:
                                  ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(C.data_ptr()), k_cap,
                                  ctypes.byref(k), ctypes.byref(st), *self._ws()), "qtn_tsvd")
         return U[:, :k.value], C[:k.value], _stats(st)
+
+    def kron_interleave(self, x: MPS, y: MPS, out: MPS) -> MPS:
+        _check(self.lib.qtn_kron_interleave(self.ctx, ctypes.byref(x.c), ctypes.byref(y.c), ctypes.byref(out.c)),
+               "qtn_kron_interleave")
+        return out
+
+    def add(self, a: MPS, b: MPS, out: MPS) -> MPS:
+        _check(self.lib.qtn_add(self.ctx, ctypes.byref(a.c), ctypes.byref(b.c), ctypes.byref(out.c)), "qtn_add")
+        return out
+
+    def launch_count(self) -> int:
+        return int(self.lib.qtn_launch_count())
+
+    def profile(self, enable: bool):
+        _check(self.lib.qtn_profile(self.ctx, int(enable), *self._ws()), "qtn_profile")
+
+    def profile_read(self, kernel_class: int):
+        """(total ms, launches, algorithmic FLOPs) of a kernel class: 0 GEMM, 1 eigensolver."""
+        ms, n, fl = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
+        _check(self.lib.qtn_profile_read(self.ctx, kernel_class, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl),
+                                         *self._ws()), "qtn_profile_read")
+        return ms.value, n.value, fl.value
 
     def amplitudes(self, psi: MPS, digits: torch.Tensor) -> torch.Tensor:
         digits = digits.to(device="cuda", dtype=torch.int32).contiguous()

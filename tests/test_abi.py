@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def declared_symbols():
     text = open(os.path.join(ROOT, "include", "qtn.h")).read()
-    decl = r"^\s*(?:qtn_status|const\s+char\s*\*|int)\s+(qtn_[a-z_0-9]+)\s*\("
+    decl = r"^\s*(?:qtn_status|const\s+char\s*\*|int|long\s+long)\s+(qtn_[a-z_0-9]+)\s*\("
     return sorted(set(re.findall(decl, text, flags=re.MULTILINE)))
 
 

@@ -84,11 +84,12 @@ def test_qft_mpo_matches_bit_reversed_dft(eng, n):
     Q = eng.build_qft_mpo(n, False, 1e-14)
     dense = OM.to_dense(Q.to_numpy_cores())
     ref = OM.qft_noswap_dense(n)
-    assert np.abs(dense - ref).max() < 5e-6
+    # FP32 build: n compressed layer products; operator error relative to the unitary's Frobenius norm
+    assert np.linalg.norm(dense - ref) / np.linalg.norm(ref) < 1e-4
     # FP32 factorisations keep a few more bond directions than FP64 at a 1e-14 cutoff
     assert Q.w_max <= 16
     Qi = eng.build_qft_mpo(n, True, 1e-14)
-    assert np.abs(OM.to_dense(Qi.to_numpy_cores()) - ref.conj().T).max() < 5e-6
+    assert np.linalg.norm(OM.to_dense(Qi.to_numpy_cores()) - ref.conj().T) / np.linalg.norm(ref) < 1e-4
 
 
 @pytest.mark.parametrize("n,c", [(6, 0.37), (10, 2.048), (12, 25.3 / 4096)])
@@ -200,8 +201,9 @@ def test_fresnel_step_untruncated_equals_dense(eng, lib, layout):
     st = eng.fresnel_step(psi, layout, Q, Qd, D, 1, 64, 1e-12)
     got = eng.to_dense(psi, layout, n).cpu().numpy()
     ref = OF.fresnel_dense(E.astype(np.complex128), c)
-    assert rel(got, ref) < 2e-5
-    assert abs(st.norm2 / np.linalg.norm(E.astype(np.complex128)) ** 2 - 1) < 2e-5
+    # six FP32 zip-up passes over n = 5 sites
+    assert rel(got, ref) < 5e-5
+    assert abs(st.norm2 / np.linalg.norm(E.astype(np.complex128)) ** 2 - 1) < 5e-5
 
 
 def test_fresnel_step_truncated_matches_oracle(eng, lib):
