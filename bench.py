@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--cutoff", type=float, default=1e-10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=3, help="end-to-end steps through host buffers (0 skips them)")
     return ap.parse_args()
 
 
@@ -197,6 +197,7 @@ def run_ours(args, rank, ws, local):
     launches0 = eng.launch_count()
     sampler.start()
     times = []
+    torch.cuda.nvtx.range_push("bench_timed")              # lets a profiler select the timed steps alone
     for _ in range(args.steps):
         flush.zero_()                                       # evict the L2 between timed steps
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -206,6 +207,7 @@ def run_ours(args, rank, ws, local):
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     clocks = sampler.stop()
     launches = eng.launch_count() - launches0
     barrier(ws)
@@ -225,7 +227,7 @@ def run_ours(args, rank, ws, local):
     out_bond = torch.empty_like(host_bond).pin_memory()
     e2e_psi = qtn.MPS(n, 4, chi)
     e2e_t = []
-    for it in range(max(args.e2e_steps, 1) + 1):
+    for it in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -239,7 +241,7 @@ def run_ours(args, rank, ws, local):
         e1.synchronize()
         if it > 0:
             e2e_t.append(e0.elapsed_time(e1))
-    e2e_ms = max_over_ranks(sum(e2e_t) / max(len(e2e_t), 1), ws)
+    e2e_ms = max_over_ranks(sum(e2e_t) / len(e2e_t), ws) if e2e_t else None
     h2d = host_sites.numel() * 8 + host_bond.numel() * 4
     return {
         "times": times, "total_ms": total_ms, "clocks": clocks, "launches": launches, "prof": prof,
@@ -330,8 +332,9 @@ def main():
     line["config"]["state_bonds_final"] = r["bonds"]
     line["clocks"] = r["clocks"]
     line["gpu_launches"] = r["launches"]
-    line["e2e"] = {"value": ws / (r["e2e_ms"] / 1e3), "unit": "steps/s", "h2d_bytes_per_step": r["h2d"],
-                   "d2h_bytes_per_step": r["h2d"]}
+    line["e2e"] = None if r["e2e_ms"] is None else {
+        "value": ws / (r["e2e_ms"] / 1e3), "unit": "steps/s", "h2d_bytes_per_step": r["h2d"],
+        "d2h_bytes_per_step": r["h2d"]}
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
