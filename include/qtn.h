@@ -185,6 +185,32 @@ qtn_status qtn_mpo_dagger(void* ctx, const qtn_mpo* in, qtn_mpo* out);
 qtn_status qtn_tsvd(void* ctx, const void* T, int m, int n, qtn_trunc trunc, void* U, void* C, int k_cap,
                     int* k_out, qtn_stats* stats, void* ws, size_t ws_bytes);
 
+/* qtn_tsvd for callers that cannot allocate device memory.  The paper has no
+ * counterpart to this call.  Such callers are handed only their input and
+ * output buffers: a custom-operator hook inside a host framework that owns
+ * the device memory and offers no workspace, or a deployment that budgets
+ * device memory once at start-up and forbids cudaMalloc/cudaFree afterwards
+ * (cudaFree also synchronises the whole device).
+ *   T, U, C, k_out, stats, trunc, m, n, k_cap: as for qtn_tsvd.
+ *   stream: the cudaStream_t to run on (NULL = legacy default stream) of the
+ *           current device.  No context and no workspace.
+ * Scratch: a fixed device array of QTN_NOALLOC_SCRATCH_BYTES inside the
+ * library; every GPU that loads the library holds it until the process
+ * exits.  The call makes no cudaMalloc, cudaFree or other allocating call.
+ * Limits: m <= QTN_NOALLOC_MAX_M and n <= QTN_NOALLOC_MAX_N; larger sizes
+ * return QTN_ERR_CAPACITY (and a message on stderr) before any device work.
+ * The first call on each device does a one-time set-up with that device
+ * current (it looks up the array's device address); make that first call
+ * before any stream capture.  All calls share the one array, which keeps the
+ * last call's contents: calls whose GPU work overlaps (several streams or
+ * host threads at once) race and must be serialised by the caller.
+ * The call synchronises the stream (it returns k on the host). */
+#define QTN_NOALLOC_MAX_M 256
+#define QTN_NOALLOC_MAX_N 2048
+#define QTN_NOALLOC_SCRATCH_BYTES (10 << 20)
+qtn_status qtn_tsvd_noalloc(const void* T, int m, int n, qtn_trunc trunc, void* U, void* C, int k_cap,
+                            int* k_out, qtn_stats* stats, void* stream);
+
 /* Interleaved d = 4 MPS of the separable field f(x) g(y) from the 1-D MPS
  * (d = 2, n sites each) of f and g (Sec. III: site p holds mu_p = 2 x_p + y_p,
  * so each site tensor is the Kronecker product of the two 1-D site tensors and

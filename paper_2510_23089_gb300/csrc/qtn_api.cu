@@ -1000,3 +1000,137 @@ qtn_status qtn_amplitudes(void* ctx, const qtn_mps* psi, const int* digits, int 
 }
 
 }  // extern "C"
+
+// ============================================================================ truncated SVD without allocation
+//
+// qtn_tsvd_noalloc runs the truncated SVD of qtn_tsvd with its scratch in the fixed device array below
+// instead of a caller workspace.  Every device that loads the library holds the array until the process
+// exits.  The array's name is a host-side stand-in: its device address is looked up once per device, with
+// that device current, by cudaGetSymbolAddress and handed to the kernels.
+#include <atomic>
+#include <mutex>
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[QTN_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+struct NoallocDevice {
+    void* base;
+    int sm_count;
+};
+NoallocDevice g_noalloc_dev[NOALLOC_MAX_DEVICES];
+std::atomic<bool> g_noalloc_ready[NOALLOC_MAX_DEVICES];
+std::mutex g_noalloc_mu;
+
+// Only the regions the truncated SVD touches: ledger, registers (+ permutation), the FP64 Gram, the B
+// buffer, the eigenbasis, eigenvalues/weights, the sketch Y and its basis Q, and the projected rows X.
+// Sized for m <= QTN_NOALLOC_MAX_M, n <= QTN_NOALLOC_MAX_N exactly as the general layout sizes them.
+WsLayout noalloc_layout() {
+    WsLayout L{};
+    L.n_sites = 1;
+    L.d = 1;
+    L.chi = QTN_NOALLOC_MAX_M;
+    L.w = 1;
+    L.m_cap = QTN_NOALLOC_MAX_M;
+    L.n_cap = QTN_NOALLOC_MAX_N;
+    L.p_cap = EIG_MAX;
+    L.dense = 0;
+    const size_t c8 = sizeof(float2), c16 = sizeof(double2);
+    const size_t mc = (size_t)L.m_cap, nc = (size_t)L.n_cap, pc = (size_t)L.p_cap;
+    const size_t gdim = std::max(mc, pc);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+    L.ledger = take(L_COUNT * sizeof(double) + 64 * sizeof(int));
+    L.regs = take(R_COUNT * sizeof(int) + (2 * gdim + 1024) * sizeof(int));
+    L.G64 = take(gdim * gdim * c16);
+    L.G32 = take(std::max(gdim * gdim, pc * nc) * c8);
+    L.U = take(gdim * gdim * c8);
+    L.lam = take(4 * gdim * sizeof(double));
+    L.Y = take(gdim * pc * c8);
+    L.Q = take(std::max(gdim * pc, pc * pc) * c8);
+    L.Z = take(std::max(gdim * nc, pc * pc) * c8);
+    L.total = off;
+    // regions of the zip-up and of the dense transforms: not used by the truncated SVD
+    L.T = L.P = L.carry = L.S64 = L.omega = L.X0 = L.X1 = off;
+    return L;
+}
+
+// One-time set-up of the calling thread's current device: the array's device address and the SM count.
+qtn_status noalloc_device(int dev, NoallocDevice* out) {
+    if (!g_noalloc_ready[dev].load(std::memory_order_acquire)) {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ready[dev].load(std::memory_order_relaxed)) {
+            void* ptr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess) {
+                fprintf(stderr, "qtn_tsvd_noalloc: cudaGetSymbolAddress failed on device %d: %s\n", dev,
+                        cudaGetErrorString(e));
+                return QTN_ERR_CUDA;
+            }
+            int sm = 0;
+            e = cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) {
+                fprintf(stderr, "qtn_tsvd_noalloc: cudaDeviceGetAttribute failed on device %d: %s\n", dev,
+                        cudaGetErrorString(e));
+                return QTN_ERR_CUDA;
+            }
+            g_noalloc_dev[dev] = NoallocDevice{ptr, sm};
+            g_noalloc_ready[dev].store(true, std::memory_order_release);
+        }
+    }
+    *out = g_noalloc_dev[dev];
+    return QTN_OK;
+}
+
+}  // namespace
+
+extern "C" qtn_status qtn_tsvd_noalloc(const void* T, int m, int n, qtn_trunc trunc, void* U, void* C, int k_cap,
+                                       int* k_out, qtn_stats* stats, void* stream) {
+    if (!T || !U || !C || !k_out || m < 1 || n < 1 || k_cap < 1) return QTN_ERR_ARG;
+    if (m > QTN_NOALLOC_MAX_M || n > QTN_NOALLOC_MAX_N) {
+        fprintf(stderr, "qtn_tsvd_noalloc: a %d x %d matrix exceeds the fixed scratch (m <= %d, n <= %d)\n", m, n,
+                QTN_NOALLOC_MAX_M, QTN_NOALLOC_MAX_N);
+        return QTN_ERR_CAPACITY;
+    }
+    static const WsLayout L = noalloc_layout();
+    if (L.total > (size_t)QTN_NOALLOC_SCRATCH_BYTES) return QTN_ERR_WORKSPACE;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return QTN_ERR_ARG;
+    NoallocDevice nd;
+    qtn_status st = noalloc_device(dev, &nd);
+    if (st) return st;
+    Ctx c{(cudaStream_t)stream, nd.sm_count, dev};
+    Ws w = ws_bind(nd.base, L);
+    cudaStream_t s = c.stream;
+    // The array keeps the previous call's contents.  The ledger and the registers are cleared; every other
+    // region is written before it is read (the Gram and the power-iteration sum are zeroed inside tsvd).
+    CK(cudaMemsetAsync(w.ledger, 0, L.G64 - L.ledger, s));
+    k_reset_stats<<<1, 1, 0, s>>>(w.R, w.ledger);
+    CKL();
+    k_set_reg<<<1, 1, 0, s>>>(w.R, R_M, m);
+    CKL();
+    k_set_reg<<<1, 1, 0, s>>>(w.R, R_N, n);
+    CKL();
+    k_set_reg<<<1, 1, 0, s>>>(w.R, R_P, std::min(m, EIG_MAX));
+    CKL();
+    qtn_trunc t2 = trunc;
+    if (t2.chi_max <= 0 || t2.chi_max > k_cap) t2.chi_max = k_cap;
+    TsvdIO io{(const float2*)T, dr(R_M), dr(R_N), m, (long long)n, w.Z};
+    Dim rows;
+    st = tsvd(&c, w, io, t2, k_cap, rows);
+    if (st) return st;
+    const int gld = std::max(L.m_cap, L.p_cap);
+    k_copy_cols<<<grid_for((long long)m * k_cap, 256, c.sm_count), 256, 0, s>>>(w.U, gld, ws_perm(w), (float2*)U,
+                                                                               k_cap, m, w.R);
+    CKL();
+    k_gather_rows<<<grid_for((long long)k_cap * n, 256, c.sm_count), 256, 0, s>>>(w.Z, dr(R_N), ws_perm(w),
+                                                                                  (float2*)C, dr(R_N), dr(R_N), w.R);
+    CKL();
+    int hk = 0;
+    CK(cudaMemcpyAsync(&hk, w.R + R_K, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *k_out = hk;
+    return fill_stats(&c, w, stats);
+}

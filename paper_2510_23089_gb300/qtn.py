@@ -33,7 +33,7 @@ EXPORTS = (
     "qtn_create", "qtn_destroy", "qtn_set_stream", "qtn_status_string", "qtn_version", "qtn_workspace_size",
     "qtn_encode", "qtn_build_qft_mpo", "qtn_build_phase_mpo", "qtn_mpo_dagger", "qtn_apply_mpo", "qtn_truncate",
     "qtn_fresnel_step", "qtn_to_dense", "qtn_norm2", "qtn_overlap", "qtn_amplitudes", "qtn_tsvd",
-    "qtn_kron_interleave", "qtn_add", "qtn_launch_count", "qtn_profile", "qtn_profile_read",
+    "qtn_kron_interleave", "qtn_add", "qtn_launch_count", "qtn_profile", "qtn_profile_read", "qtn_tsvd_noalloc",
 )
 
 
@@ -92,6 +92,7 @@ def load_library(path: str = LIB_PATH):
         "qtn_overlap": [P, mp, mp, ctypes.POINTER(D), P, S],
         "qtn_amplitudes": [P, mp, P, I, P, P, S],
         "qtn_tsvd": [P, P, I, I, tr, P, P, I, ctypes.POINTER(I), st, P, S],
+        "qtn_tsvd_noalloc": [P, I, I, tr, P, P, I, ctypes.POINTER(I), st, P],
         "qtn_kron_interleave": [P, mp, mp, mp],
         "qtn_add": [P, mp, mp, mp],
         "qtn_profile": [P, I, P, S],
