@@ -144,6 +144,8 @@ def build_state_gpu(qtn, n: int, chi: int, cutoff: float):
         eng.encode(torch.from_numpy(gy[r].astype(np.complex64)).cuda(), n, "1d", Y, 32, cutoff, stats=False)
         term = qtn.MPS(n, 4, big)
         eng.kron_interleave(X, Y, term)
+        # right-canonical terms keep the FP32 sweeps over the direct sum well conditioned
+        eng.truncate(term, big, 1e-13, stats=False)
         if acc is None:
             acc = term
         else:

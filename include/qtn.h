@@ -222,7 +222,11 @@ qtn_status qtn_kron_interleave(void* ctx, const qtn_mps* x, const qtn_mps* y, qt
 /* MPS of the sum |a> + |b> (block-diagonal bonds; the boundary sites are
  * concatenated).  out: same n_sites and d, chi_cap >= bond_a + bond_b at
  * every inner bond (QTN_ERR_CAPACITY otherwise); must not alias a or b.
- * Result canon NONE; compress with qtn_truncate.  The call synchronises. */
+ * Result canon NONE; compress with qtn_truncate.  The FP32 compression is
+ * accurate when a and b are in the same canonical form (right-canonical, as
+ * qtn_truncate leaves them); a left-canonical part turns the unswept
+ * environment into a non-isometry that amplifies rounding.  The call
+ * synchronises. */
 qtn_status qtn_add(void* ctx, const qtn_mps* a, const qtn_mps* b, qtn_mps* out);
 
 /* Zip-up MPO x MPS application with SVD truncation (Sec. V, Fig. fig_mpo).

@@ -123,6 +123,14 @@ __global__ void k_path(Dim mdim, int* __restrict__ R, double* __restrict__ ledge
     R[R_RAND] = (m > EIG_MAX) ? 1 : 0;
     R[R_P] = min(m, EIG_MAX);
     R[R_ROWS] = min(m, EIG_MAX);
+    R[R_DEP] = 0;
+    R[R_PI] = 0;
+}
+
+// The power iteration of the range finder runs only for a full-rank sketch: when the sketch already has
+// dependent columns, the rank of T is below the subspace size and the sketch spans the range of T.
+__global__ void k_set_pi(int* __restrict__ R) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) R[R_PI] = (R[R_RAND] == 1 && R[R_DEP] == 0) ? 1 : 0;
 }
 
 // |T|_F^2 in FP64 accumulated into ledger[L_TRACE] (range-finder path: the total weight of the factorised
@@ -156,8 +164,8 @@ __global__ void k_total_weight(const float2* __restrict__ T, Dim ldt, Dim mdim, 
 
 // Column norms of a row-major m x ld matrix (columns [0, ncols)) -> out (FP32 norms).
 __global__ void k_col_norms(const float2* __restrict__ Q, int ld, Dim mdim, Dim ncols, float* __restrict__ out,
-                            const int* __restrict__ R) {
-    if (R[R_RAND] != 1) return;
+                            const int* __restrict__ R, int greg) {
+    if (R[greg] != 1) return;
     const int m = mdim.eval(R), nc = ncols.eval(R);
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -172,12 +180,20 @@ __global__ void k_col_norms(const float2* __restrict__ Q, int ld, Dim mdim, Dim 
     }
 }
 
-// pre[c]: norm of column c before any projection; a column whose residual falls below 1e-5 of it is
-// numerically dependent on the columns already orthonormalised and is set to zero.
+// Orthonormalisation of one block of NB columns against each other (classical Gram-Schmidt, two passes),
+// after the block has been projected against the finished blocks.  The range finder runs it twice per
+// block (block CGS2): the first run (decide = 1) finds dependent columns, the second (decide = 0), after a
+// second projection against the finished blocks, restores orthogonality lost to the cancellation in the
+// first.  pre[c]: norm of column c before any projection; in the first run a column whose residual falls
+// below CGS_DEP of it is numerically dependent on the columns already orthonormalised, is set to zero and
+// raises R[R_DEP].  The block runs only when R[greg] == 1.
+constexpr float CGS_DEP = 1e-5f;
+
 template <int NB, int MAXM>
 __device__ __forceinline__ void cgs_block_body(float2* __restrict__ Q, int ld, Dim mdim, int c0,
-                                               const float* __restrict__ pre, const int* __restrict__ R) {
-    if (R[R_RAND] != 1) return;
+                                               const float* __restrict__ pre, int* __restrict__ R, int greg,
+                                               int decide) {
+    if (R[greg] != 1) return;
     extern __shared__ float2 S[];              // column-major, S[c * MAXM + row]
     __shared__ float cr_s[NB], ci_s[NB], red[32];
     __shared__ float nrm;
@@ -202,13 +218,18 @@ __device__ __forceinline__ void cgs_block_body(float2* __restrict__ Q, int ld, D
         __syncthreads();
         return nrm;
     };
+    bool dep = false;
     for (int c = 0; c < NB; ++c) {
         float2* w = S + c * MAXM;
         const float nraw = norm_of(w);
-        const float n0 = (nraw > 1e-5f * pre[c0 + c]) ? nraw : 0.f;   // dependent on earlier blocks
+        // first run: dependent on the finished blocks when the projection left less than CGS_DEP of the
+        // column; second run: the column was a unit vector, so a re-projection that removes half of it means
+        // the first result was rounding, not a direction (Kahan-Parlett "twice is enough")
+        const float n0 = decide ? ((nraw > CGS_DEP * pre[c0 + c]) ? nraw : 0.f) : ((nraw > 0.5f) ? nraw : 0.f);
         const float inv0 = n0 > 0.f ? 1.f / n0 : 0.f;
         for (int row = tid; row < m; row += blockDim.x) w[row] = cscale(w[row], inv0);
         __syncthreads();
+        float a1 = 1.f, na = 0.f;
         for (int pass = 0; pass < 2 && n0 > 0.f; ++pass) {
             for (int q = warp; q < c; q += blockDim.x / 32) {
                 const float2* u = S + q * MAXM;
@@ -235,25 +256,41 @@ __device__ __forceinline__ void cgs_block_body(float2* __restrict__ Q, int ld, D
                 w[row] = acc;
             }
             __syncthreads();
+            if (pass == 0) a1 = norm_of(w);
+            else na = norm_of(w);
         }
-        const float na = norm_of(w);
-        const float sc = (n0 > 0.f && na > 1e-5f) ? 1.f / na : 0.f;
+        // the second in-block pass must not cancel either: otherwise the residual is rounding
+        const float sc = (n0 > 0.f && na > CGS_DEP && na > 0.5f * a1) ? 1.f / na : 0.f;
+        if (!(sc > 0.f) && (decide ? pre[c0 + c] > 0.f : nraw > 0.f)) dep = true;
         for (int row = tid; row < m; row += blockDim.x) w[row] = cscale(w[row], sc);
         __syncthreads();
     }
+    if (tid == 0 && dep) R[R_DEP] = 1;
     for (int e = tid; e < m * NB; e += blockDim.x) {
         const int row = e / NB, c = e % NB;
         Q[(long long)row * ld + c0 + c] = S[c * MAXM + row];
     }
 }
 
-__global__ void __launch_bounds__(1024) k_cgs_block_32(float2* Q, int ld, Dim mdim, int c0, const float* pre,
-                                                       const int* R) {
-    cgs_block_body<32, 512>(Q, ld, mdim, c0, pre, R);
+__global__ void __launch_bounds__(1024) k_cgs_block_32(float2* Q, int ld, Dim mdim, int c0, const float* pre, int* R,
+                                                      int greg, int decide) {
+    cgs_block_body<32, 512>(Q, ld, mdim, c0, pre, R, greg, decide);
 }
-__global__ void __launch_bounds__(1024) k_cgs_block_16(float2* Q, int ld, Dim mdim, int c0, const float* pre,
-                                                       const int* R) {
-    cgs_block_body<16, 1024>(Q, ld, mdim, c0, pre, R);
+__global__ void __launch_bounds__(1024) k_cgs_block_16(float2* Q, int ld, Dim mdim, int c0, const float* pre, int* R,
+                                                      int greg, int decide) {
+    cgs_block_body<16, 1024>(Q, ld, mdim, c0, pre, R, greg, decide);
+}
+__global__ void __launch_bounds__(1024) k_cgs_block_8(float2* Q, int ld, Dim mdim, int c0, const float* pre, int* R,
+                                                      int greg, int decide) {
+    cgs_block_body<8, 2048>(Q, ld, mdim, c0, pre, R, greg, decide);
+}
+
+// Guarded copy of n elements (runs when R[greg] == gval).
+__global__ void k_copy_guarded(const float2* __restrict__ src, float2* __restrict__ dst, long long n,
+                               const int* __restrict__ R, int greg, int gval) {
+    if (R[greg] != gval) return;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        dst[e] = src[e];
 }
 
 // Squared norms of the rows of X (FP64 accumulation): w[i] = sum_c |X[i, c]|^2.
@@ -297,12 +334,12 @@ __global__ void k_select(const double* __restrict__ w, Dim rdim, int chi_max, do
     __syncthreads();
     if (threadIdx.x == 0) {
         // total weight: the sum of all projected weights when the basis spans the whole row space (the same
-        // FP32 projections as the kept weights, so the discarded weight is consistent), else the Gram trace
-        double total = ledger[L_TRACE];
-        if (total_from_weights) {
-            total = 0.0;
-            for (int i = r - 1; i >= 0; --i) total += sorted_w[i];
-        }
+        // FP32 projections as the kept weights, so the discarded weight is consistent); on the range-finder
+        // path the exact |T|^2, which also counts the weight outside the sketch, unless the FP32 projections
+        // over-count it (their sum then takes its place, so the tail is never consumed by rounding)
+        double wsum = 0.0;
+        for (int i = r - 1; i >= 0; --i) wsum += sorted_w[i];
+        const double total = total_from_weights ? wsum : fmax(ledger[L_TRACE], wsum);
         double kept = 0.0;
         int k = 0;
         // directions whose captured weight is below NULL_FLOOR * total are numerically null for FP32 data

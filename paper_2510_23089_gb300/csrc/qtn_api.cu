@@ -23,9 +23,12 @@ __global__ void k_stage2(const float2*, float2*, const float2*, int, int, int, i
 __global__ void k_trace(const double2*, int, Dim, int*, double*);
 __global__ void k_path(Dim, int*, double*);
 __global__ void k_total_weight(const float2*, Dim, Dim, Dim, const int*, double*);
-__global__ void k_cgs_block_32(float2*, int, Dim, int, const float*, const int*);
-__global__ void k_cgs_block_16(float2*, int, Dim, int, const float*, const int*);
-__global__ void k_col_norms(const float2*, int, Dim, Dim, float*, const int*);
+__global__ void k_cgs_block_32(float2*, int, Dim, int, const float*, int*, int, int);
+__global__ void k_cgs_block_16(float2*, int, Dim, int, const float*, int*, int, int);
+__global__ void k_cgs_block_8(float2*, int, Dim, int, const float*, int*, int, int);
+__global__ void k_col_norms(const float2*, int, Dim, Dim, float*, const int*, int);
+__global__ void k_set_pi(int*);
+__global__ void k_copy_guarded(const float2*, float2*, long long, const int*, int, int);
 __global__ void k_kron_interleave(const float2*, const int*, int, const float2*, const int*, int, float2*, int*, int,
                                   int);
 __global__ void k_direct_sum(const float2*, const int*, int, const float2*, const int*, int, float2*, int*, int, int,
@@ -237,7 +240,6 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
     //      U = Q U_B.  No product with G is ever formed, so the FP32 dynamic range is that of T itself.
     if (mc > EIG_MAX) {
         if (mc > CGS_MAXM_ALL) return QTN_ERR_WORKSPACE;
-        const int CGS_B = (mc <= 512) ? 32 : 16;
         const Dim P = dr(R_P);
         k_total_weight<<<grid_for((long long)mc * ncap, 256, c->sm_count), 256, 0, s>>>(io.T, io.n, io.m, io.n,
                                                                                             w.R, w.ledger);
@@ -256,65 +258,107 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
             CK(launch_gemm(g, mc, pc, ncap, w.R, s));
         }
         static bool cgs_configured = false;
-        const size_t cgs_smem = (size_t)32 * 512 * sizeof(float2);   // = 16 x 1024 as well
+        const size_t cgs_smem = (size_t)32 * 512 * sizeof(float2);   // = 16 x 1024 = 8 x 2048 as well
         if (!cgs_configured) {
             CK(cudaFuncSetAttribute(k_cgs_block_32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cgs_smem));
             CK(cudaFuncSetAttribute(k_cgs_block_16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cgs_smem));
+            CK(cudaFuncSetAttribute(k_cgs_block_8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cgs_smem));
             cgs_configured = true;
         }
-        // orthonormalise the p columns of Yb in place (block classical Gram-Schmidt, twice)
-        auto block_orth = [&](float2* Yb) -> qtn_status {
-            k_col_norms<<<grid_for((long long)pc * 32, 256, c->sm_count), 256, 0, s>>>(Yb, pc, io.m, P, pre, w.R);
+        // orthonormalise the p columns of Yb (rows live `rows`, at most rows_cap) in place by block classical
+        // Gram-Schmidt with reorthogonalisation: each block is projected against the finished blocks and
+        // orthonormalised internally, twice; runs when R[greg] == 1
+        auto block_orth = [&](float2* Yb, Dim rows, int rows_cap, int greg) -> qtn_status {
+            const int CGS_B = (rows_cap <= 512) ? 32 : (rows_cap <= 1024 ? 16 : 8);
+            k_col_norms<<<grid_for((long long)pc * 32, 256, c->sm_count), 256, 0, s>>>(Yb, pc, rows, P, pre, w.R,
+                                                                                      greg);
             CKL();
             for (int b0 = 0; b0 < pc; b0 += CGS_B) {
-                for (int pass = 0; b0 > 0 && pass < 2; ++pass) {   // project out the finished blocks
-                    GemmDesc g{};                                   // Cb = Q[:, :b0]^dagger Y[:, b0:b0+B]
-                    g.A = mat(Yb, dc(1), dc(pc), 1);
-                    g.B = mat(Yb + b0, dc(pc), dc(1));
-                    g.C = w.Z; g.crs = dc(CGS_B); g.ccs = dc(1);
-                    g.M = dc(b0); g.N = dc(CGS_B); g.K = io.m;
-                    g.guard_reg = R_RAND; g.guard_val = 1;
-                    CK(launch_gemm(g, b0, CGS_B, mc, w.R, s));
-                    GemmDesc h{};                                   // Y[:, b0:b0+B] -= Q[:, :b0] Cb
-                    h.A = mat(Yb, dc(pc), dc(1));
-                    h.B = mat(w.Z, dc(CGS_B), dc(1));
-                    h.C = Yb + b0; h.crs = dc(pc); h.ccs = dc(1);
-                    h.M = io.m; h.N = dc(CGS_B); h.K = dc(b0);
-                    h.mode = OUT_ACCUM; h.alpha_re = -1.f;
-                    h.guard_reg = R_RAND; h.guard_val = 1;
-                    CK(launch_gemm(h, mc, CGS_B, b0, w.R, s));
+                for (int pass = 0; pass < (b0 > 0 ? 2 : 1); ++pass) {
+                    if (b0 > 0) {
+                        GemmDesc g{};                               // Cb = Q[:, :b0]^dagger Y[:, b0:b0+B]
+                        g.A = mat(Yb, dc(1), dc(pc), 1);
+                        g.B = mat(Yb + b0, dc(pc), dc(1));
+                        g.C = w.Z; g.crs = dc(CGS_B); g.ccs = dc(1);
+                        g.M = dc(b0); g.N = dc(CGS_B); g.K = rows;
+                        g.guard_reg = greg; g.guard_val = 1;
+                        CK(launch_gemm(g, b0, CGS_B, rows_cap, w.R, s));
+                        GemmDesc h{};                               // Y[:, b0:b0+B] -= Q[:, :b0] Cb
+                        h.A = mat(Yb, dc(pc), dc(1));
+                        h.B = mat(w.Z, dc(CGS_B), dc(1));
+                        h.C = Yb + b0; h.crs = dc(pc); h.ccs = dc(1);
+                        h.M = rows; h.N = dc(CGS_B); h.K = dc(b0);
+                        h.mode = OUT_ACCUM; h.alpha_re = -1.f;
+                        h.guard_reg = greg; h.guard_val = 1;
+                        CK(launch_gemm(h, rows_cap, CGS_B, b0, w.R, s));
+                    }
+                    const int decide = (pass == 0);
+                    if (CGS_B == 32) k_cgs_block_32<<<1, 1024, cgs_smem, s>>>(Yb, pc, rows, b0, pre, w.R, greg, decide);
+                    else if (CGS_B == 16)
+                        k_cgs_block_16<<<1, 1024, cgs_smem, s>>>(Yb, pc, rows, b0, pre, w.R, greg, decide);
+                    else k_cgs_block_8<<<1, 1024, cgs_smem, s>>>(Yb, pc, rows, b0, pre, w.R, greg, decide);
+                    CKL();
                 }
-                if (CGS_B == 32) k_cgs_block_32<<<1, 1024, cgs_smem, s>>>(Yb, pc, io.m, b0, pre, w.R);
-                else k_cgs_block_16<<<1, 1024, cgs_smem, s>>>(Yb, pc, io.m, b0, pre, w.R);
-                CKL();
             }
             return QTN_OK;
         };
-        if ((st = block_orth(w.Y))) return st;
-        // one power iteration, Y' = T (T^dagger Q), accumulated over column chunks of T
-        CK(cudaMemsetAsync(w.Q, 0, (size_t)mc * pc * sizeof(float2), s));
-        for (long long c0 = 0; c0 < io.n_cap; c0 += cw) {
-            const int cwid = (int)std::min<long long>(cw, io.n_cap - c0);
-            const Dim ncol = one_chunk ? io.n : dc(cwid);
-            GemmDesc g{};                                           // Z1 = T_c^dagger Q  (cw x p) in the B buffer
-            g.A = mat(io.T + c0, dc(1), io.n, 1);
-            g.B = mat(w.Y, dc(pc), dc(1));
-            g.C = w.G32; g.crs = dc(pc); g.ccs = dc(1);
-            g.M = ncol; g.N = P; g.K = io.m;
-            g.guard_reg = R_RAND; g.guard_val = 1;
-            CK(launch_gemm(g, cwid, pc, mc, w.R, s));
-            GemmDesc h{};                                           // Y' += T_c Z1
-            h.A = mat(io.T + c0, io.n, dc(1));
-            h.B = mat(w.G32, dc(pc), dc(1));
-            h.C = w.Q; h.crs = dc(pc); h.ccs = dc(1);
-            h.M = io.m; h.N = P; h.K = ncol;
-            h.mode = OUT_ACCUM;
-            h.guard_reg = R_RAND; h.guard_val = 1;
-            CK(launch_gemm(h, mc, pc, cwid, w.R, s));
+        if ((st = block_orth(w.Y, io.m, mc, R_RAND))) return st;
+        // Power iteration, only for a full-rank sketch (otherwise the sketch already spans the range of T).
+        // Each product with T or T^dagger is orthonormalised before the next, so a direction is never
+        // represented at the square of its relative singular value.
+        k_set_pi<<<1, 1, 0, s>>>(w.R);
+        CKL();
+        if (one_chunk && ncap <= 2048) {   // Z fits the B buffer whole and the block orthonormaliser
+            {   // Z = T^dagger Q (n x p) in the B buffer
+                GemmDesc g{};
+                g.A = mat(io.T, dc(1), io.n, 1);
+                g.B = mat(w.Y, dc(pc), dc(1));
+                g.C = w.G32; g.crs = dc(pc); g.ccs = dc(1);
+                g.M = io.n; g.N = P; g.K = io.m;
+                g.guard_reg = R_PI; g.guard_val = 1;
+                CK(launch_gemm(g, ncap, pc, mc, w.R, s));
+            }
+            if ((st = block_orth(w.G32, io.n, ncap, R_PI))) return st;
+            {   // Y = T Z
+                GemmDesc g{};
+                g.A = mat(io.T, io.n, dc(1));
+                g.B = mat(w.G32, dc(pc), dc(1));
+                g.C = w.Y; g.crs = dc(pc); g.ccs = dc(1);
+                g.M = io.m; g.N = P; g.K = io.n;
+                g.guard_reg = R_PI; g.guard_val = 1;
+                CK(launch_gemm(g, mc, pc, ncap, w.R, s));
+            }
+            if ((st = block_orth(w.Y, io.m, mc, R_PI))) return st;
+        } else {
+            // T too wide for the intermediate: Y' = T (T^dagger Q) accumulated over column chunks of T
+            CK(cudaMemsetAsync(w.Q, 0, (size_t)mc * pc * sizeof(float2), s));
+            for (long long c0 = 0; c0 < io.n_cap; c0 += cw) {
+                const int cwid = (int)std::min<long long>(cw, io.n_cap - c0);
+                const Dim ncol = one_chunk ? io.n : dc(cwid);
+                GemmDesc g{};                                       // Z1 = T_c^dagger Q  (cw x p) in the B buffer
+                g.A = mat(io.T + c0, dc(1), io.n, 1);
+                g.B = mat(w.Y, dc(pc), dc(1));
+                g.C = w.G32; g.crs = dc(pc); g.ccs = dc(1);
+                g.M = ncol; g.N = P; g.K = io.m;
+                g.guard_reg = R_PI; g.guard_val = 1;
+                CK(launch_gemm(g, cwid, pc, mc, w.R, s));
+                GemmDesc h{};                                       // Y' += T_c Z1
+                h.A = mat(io.T + c0, io.n, dc(1));
+                h.B = mat(w.G32, dc(pc), dc(1));
+                h.C = w.Q; h.crs = dc(pc); h.ccs = dc(1);
+                h.M = io.m; h.N = P; h.K = ncol;
+                h.mode = OUT_ACCUM;
+                h.guard_reg = R_PI; h.guard_val = 1;
+                CK(launch_gemm(h, mc, pc, cwid, w.R, s));
+            }
+            if ((st = block_orth(w.Q, io.m, mc, R_PI))) return st;
+            k_copy_guarded<<<grid_for((long long)mc * pc, 256, c->sm_count), 256, 0, s>>>(w.Q, w.Y,
+                                                                                       (long long)mc * pc, w.R,
+                                                                                       R_PI, 1);
+            CKL();
         }
-        if ((st = block_orth(w.Q))) return st;
-        float2* Qb = w.Q;          // orthonormal basis of the sketch
-        float2* UB = w.Y;          // eigenvectors of the Gram of B (p x p, column-major)
+        float2* Qb = w.Y;          // orthonormal basis of the sketch
+        float2* UB = w.Q;          // eigenvectors of the Gram of B (p x p, column-major)
         // Gram of B = Q^dagger T accumulated over column chunks of T that fit the B buffer (B is never
         // needed whole: X is formed from T and U directly)
         CK(cudaMemsetAsync(w.G64, 0, (size_t)pc * gld * sizeof(double2), s));

@@ -70,6 +70,8 @@ enum Reg : int {
     R_MAXBOND = 22,
     R_RAND = 23,   // 1 when the current factorisation takes the range-finder path (m > EIG_MAX)
     R_ROWS = 24,   // rows of the projected matrix U^dagger T (m, or the subspace size)
+    R_DEP = 25,    // range finder: 1 when the sketch has dependent columns (rank below the subspace size)
+    R_PI = 26,     // range finder: 1 when the power iteration runs (full-rank sketch)
     R_COUNT = 32
 };
 
