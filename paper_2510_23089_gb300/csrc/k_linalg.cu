@@ -143,7 +143,10 @@ cudaError_t launch_gemm(const GemmDesc& d, int max_m, int max_n, int max_k, cons
 constexpr int EIG_THREADS = 1024;
 constexpr int EIG_GL = 8;                       // lanes per column pair
 constexpr int EIG_GROUPS = EIG_THREADS / EIG_GL;
-constexpr int EIG_RS = EIG_MAX + 4;             // padded column stride in shared memory
+constexpr int EIG_RS = EIG_MAX + 1;             // odd column stride: strided column reads hit distinct banks
+constexpr int EIG_CB = 16;                      // columns per block of the re-orthonormalisation
+constexpr int EIG_QC = EIG_THREADS / 32;        // finished columns per projection chunk (one per warp)
+constexpr float EIG_DEP0 = 1e-3f;               // residual below which a column is dependent (first run)
 constexpr float EIG_TOL = 1.0e-6f;
 constexpr float EIG_NOISE = 1.0e-13f;           // |w_i| |w_j| floor (matrix scaled to unit largest diagonal)
 
@@ -269,92 +272,187 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
         lam[rk] = v;
     }
     __syncthreads();
-    // Re-orthonormalise the columns in descending-eigenvalue order (classical Gram-Schmidt, two passes):
-    // directions below the FP32 resolution of G are not orthogonal to working precision after Jacobi, and
-    // the new site must be an isometry.  A column that turns out numerically dependent on the previous
-    // ones is replaced by a pseudo-random vector orthogonalised the same way, so the basis stays complete
-    // and no weight of the factorised matrix is lost.
+    // Re-orthonormalise the columns in descending-eigenvalue order: Jacobi leaves the directions below the
+    // FP32 resolution of G non-orthogonal, and the new site must be an isometry.  Blocks of EIG_CB unit
+    // columns are projected on the finished columns and orthonormalised internally by Cholesky QR, twice
+    // (the second run restores what cancellation took from the first).  A column whose residual falls below
+    // EIG_DEP0 in the first run, or loses half of itself in the second, is numerically dependent: it is set
+    // aside and replaced at the end by a pseudo-random vector orthonormalised the same way, so the basis
+    // stays complete and no weight of the factorised matrix is lost.
     __shared__ int col_of_rank[EIG_MAX];
-    __shared__ float coef_r[EIG_MAX], coef_i[EIG_MAX];
-    __shared__ float red_s[32];
-    __shared__ float nrm_cur;
-    for (int j = tid; j < r; j += EIG_THREADS) col_of_rank[rank_of[j]] = j;
-    __syncthreads();
+    __shared__ unsigned char dead[EIG_MAX];          // by rank
+    __shared__ float invn[EIG_MAX];
+    __shared__ float2 Cs[EIG_QC * EIG_CB];           // projection coefficients (finished chunk x block)
+    __shared__ float2 Rb[EIG_CB * EIG_CB];           // Gram of the block, overwritten by its Cholesky factor
+    __shared__ unsigned char bdead[EIG_CB];
+    __shared__ int nlive_s;
     const int warp = tid / 32, wl = tid % 32;
-    auto block_norm = [&](float2* w) {
-        float ss = 0.f;
-        for (int row = tid; row < r; row += EIG_THREADS) ss += w[row].x * w[row].x + w[row].y * w[row].y;
-        for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
-        if (wl == 0) red_s[warp] = ss;
-        __syncthreads();
-        if (tid == 0) {
-            float tot = 0.f;
-            for (int q = 0; q < EIG_THREADS / 32; ++q) tot += red_s[q];
-            nrm_cur = sqrtf(tot);
-        }
-        __syncthreads();
-        return nrm_cur;
-    };
-    // w -= sum_{q<t} (u_q^dagger w) u_q: coefficients by warps (one dot per warp), then every warp updates a
-    // slice of rows with its lanes splitting the q-sum (all 1024 threads busy).
-    auto project_out = [&](float2* w, int t) {
-        for (int q = warp; q < t; q += EIG_THREADS / 32) {
-            const float2* u = W + col_of_rank[q] * EIG_RS;
-            float cr = 0.f, ci = 0.f;
-            for (int row = wl; row < r; row += 32) {
-                float2 a = u[row], b = w[row];
-                cr = fmaf(a.x, b.x, fmaf(a.y, b.y, cr));
-                ci = fmaf(a.x, b.y, fmaf(-a.y, b.x, ci));
-            }
-            for (int off = 16; off > 0; off >>= 1) {
-                cr += __shfl_xor_sync(0xffffffffu, cr, off);
-                ci += __shfl_xor_sync(0xffffffffu, ci, off);
-            }
-            if (wl == 0) { coef_r[q] = cr; coef_i[q] = ci; }
-        }
-        __syncthreads();
-        for (int row = warp; row < r; row += EIG_THREADS / 32) {
-            float ar = 0.f, ai = 0.f;
-            for (int q = wl; q < t; q += 32) {
-                const float2 u = W[col_of_rank[q] * EIG_RS + row];
-                ar += coef_r[q] * u.x - coef_i[q] * u.y;
-                ai += coef_r[q] * u.y + coef_i[q] * u.x;
-            }
-            for (int off = 16; off > 0; off >>= 1) {
-                ar += __shfl_xor_sync(0xffffffffu, ar, off);
-                ai += __shfl_xor_sync(0xffffffffu, ai, off);
-            }
-            if (wl == 0) w[row] = make_float2(w[row].x - ar, w[row].y - ai);
-        }
-        __syncthreads();
-    };
-    auto scale_col = [&](float2* w, float sc) {
-        for (int row = tid; row < r; row += EIG_THREADS) w[row] = cscale(w[row], sc);
-        __syncthreads();
-    };
-    // The Jacobi columns are orthogonal to the solve's tolerance, so one classical pass restores working
-    // precision; a second pass runs when the projection cancelled most of the column ("twice is enough").
-    // A column found dependent gets a pseudo-random replacement.
-    for (int t = 0; t < r; ++t) {
-        float2* w = W + col_of_rank[t] * EIG_RS;
-        for (int attempt = 0; attempt < 2; ++attempt) {
-            if (attempt == 1) {
-                for (int row = tid; row < r; row += EIG_THREADS) w[row] = gauss2(977 + t, row, t);
+    for (int j = tid; j < r; j += EIG_THREADS) {
+        col_of_rank[rank_of[j]] = j;
+        const double nj = nrm[j] / gscale;           // column norm in the units of W
+        invn[j] = nj > 0.0 ? (float)(1.0 / nj) : 0.f;
+        dead[rank_of[j]] = !(nj > 0.0);
+    }
+    __syncthreads();
+    for (int e = tid; e < r * r; e += EIG_THREADS) {
+        const int j = e / r, row = e % r;
+        W[j * EIG_RS + row] = cscale(W[j * EIG_RS + row], invn[j]);
+    }
+    __syncthreads();
+    auto ortho_block = [&](int t0, int nb) {
+        for (int pass = 0; pass < 2; ++pass) {
+            // projection on the finished columns (ranks < t0), EIG_QC of them at a time
+            for (int qc = 0; qc < t0; qc += EIG_QC) {
+                const int nq = min(EIG_QC, t0 - qc);
+                if (warp < nq) {
+                    const float2* wq = W + col_of_rank[qc + warp] * EIG_RS;
+                    const int c = wl & 15, h = wl >> 4;
+                    float2 acc = make_float2(0.f, 0.f);
+                    if (c < nb) {
+                        const float2* wc = W + col_of_rank[t0 + c] * EIG_RS;
+                        for (int row = h; row < r; row += 2) {
+                            const float2 x = wq[row], y = wc[row];   // conj(x) * y
+                            acc.x = fmaf(x.x, y.x, fmaf(x.y, y.y, acc.x));
+                            acc.y = fmaf(x.x, y.y, fmaf(-x.y, y.x, acc.y));
+                        }
+                    }
+                    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
+                    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
+                    if (h == 0 && c < nb) Cs[warp * EIG_CB + c] = acc;
+                }
+                __syncthreads();
+                for (int e = tid; e < r * nb; e += EIG_THREADS) {
+                    const int c = e / r, row = e % r;
+                    float2* wc = W + col_of_rank[t0 + c] * EIG_RS;
+                    float2 acc = wc[row];
+                    for (int q = 0; q < nq; ++q) {
+                        const float2 u = W[col_of_rank[qc + q] * EIG_RS + row], k = Cs[q * EIG_CB + c];
+                        acc.x -= u.x * k.x - u.y * k.y;
+                        acc.y -= u.x * k.y + u.y * k.x;
+                    }
+                    wc[row] = acc;
+                }
                 __syncthreads();
             }
-            const float n0 = block_norm(w);
-            if (!(n0 > 0.f)) continue;
-            scale_col(w, 1.f / n0);
-            project_out(w, t);
-            float na = block_norm(w);
-            if (na < 0.7f) {   // heavy cancellation: a second classical pass restores orthogonality
-                project_out(w, t);
-                na = block_norm(w);
+            // Gram of the block (upper triangle), one warp per entry
+            for (int p = warp; p < nb * nb; p += EIG_THREADS / 32) {
+                const int c1 = p / nb, c2 = p % nb;
+                if (c2 < c1) continue;
+                const float2* x = W + col_of_rank[t0 + c1] * EIG_RS;
+                const float2* y = W + col_of_rank[t0 + c2] * EIG_RS;
+                float sr = 0.f, si = 0.f;
+                for (int row = wl; row < r; row += 32) {
+                    const float2 u = x[row], v = y[row];
+                    sr = fmaf(u.x, v.x, fmaf(u.y, v.y, sr));
+                    si = fmaf(u.x, v.y, fmaf(-u.y, v.x, si));
+                }
+                for (int off = 16; off > 0; off >>= 1) {
+                    sr += __shfl_xor_sync(0xffffffffu, sr, off);
+                    si += __shfl_xor_sync(0xffffffffu, si, off);
+                }
+                if (wl == 0) Rb[c1 * EIG_CB + c2] = make_float2(sr, si);
             }
-            if (na > 1e-4f) { scale_col(w, 1.f / na); break; }
-            if (attempt == 1) scale_col(w, 0.f);
+            __syncthreads();
+            // Cholesky factor (upper, row c of Rb), one warp; a pivot below the threshold marks the column
+            // dependent (first run: relative residual EIG_DEP0 of a unit column; second run: half of it)
+            if (warp == 0) {
+                const float thr2 = pass == 0 ? EIG_DEP0 * EIG_DEP0 : 0.25f;
+                for (int c = 0; c < nb; ++c) {
+                    float d = Rb[c * EIG_CB + c].x;
+                    for (int k = 0; k < c; ++k) {
+                        const float2 v = Rb[k * EIG_CB + c];
+                        d -= v.x * v.x + v.y * v.y;
+                    }
+                    const bool dc = bdead[c] || !(d > thr2);
+                    __syncwarp();                            // every lane has read the pivot row
+                    if (dc) {
+                        if (wl >= c && wl < nb) Rb[c * EIG_CB + wl] = make_float2(0.f, 0.f);
+                        if (wl == 0) bdead[c] = 1;
+                    } else {
+                        const float rcc = sqrtf(d), inv = 1.f / rcc;
+                        if (wl > c && wl < nb) {
+                            float2 v = Rb[c * EIG_CB + wl];
+                            for (int k = 0; k < c; ++k) {
+                                const float2 a = Rb[k * EIG_CB + c], b = Rb[k * EIG_CB + wl];   // conj(a) * b
+                                v.x -= a.x * b.x + a.y * b.y;
+                                v.y -= a.x * b.y - a.y * b.x;
+                            }
+                            Rb[c * EIG_CB + wl] = cscale(v, inv);
+                        }
+                        __syncwarp();
+                        if (wl == 0) Rb[c * EIG_CB + c] = make_float2(rcc, 0.f);
+                    }
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+            // block <- block R^{-1} by forward substitution in place, one row per thread (dependent columns
+            // become zero)
+            for (int row = tid; row < r; row += EIG_THREADS) {
+                for (int c = 0; c < nb; ++c) {
+                    float2* wc = W + col_of_rank[t0 + c] * EIG_RS + row;
+                    float2 v = *wc;
+                    for (int k = 0; k < c; ++k) {
+                        const float2 xk = W[col_of_rank[t0 + k] * EIG_RS + row], rk = Rb[k * EIG_CB + c];
+                        v.x -= xk.x * rk.x - xk.y * rk.y;
+                        v.y -= xk.x * rk.y + xk.y * rk.x;
+                    }
+                    *wc = bdead[c] ? make_float2(0.f, 0.f) : cscale(v, 1.f / Rb[c * EIG_CB + c].x);
+                }
+            }
+            __syncthreads();
         }
+    };
+    for (int t0 = 0; t0 < r; t0 += EIG_CB) {
+        const int nb = min(EIG_CB, r - t0);
+        if (tid < EIG_CB) bdead[tid] = (tid < nb) ? dead[t0 + tid] : 1;
+        __syncthreads();
+        ortho_block(t0, nb);
+        if (tid < nb) dead[t0 + tid] = bdead[tid];
+        __syncthreads();
     }
+    // completion: dependent ranks move to the end (stable), get pseudo-random unit vectors and are
+    // orthonormalised against every column before them
+    if (tid == 0) {                                   // rank_of serves as scratch; it is rewritten below
+        int nl = 0;
+        for (int t = 0; t < r; ++t)
+            if (!dead[t]) rank_of[nl++] = col_of_rank[t];
+        int nd = nl;
+        for (int t = 0; t < r; ++t)
+            if (dead[t]) rank_of[nd++] = col_of_rank[t];
+        for (int t = 0; t < r; ++t) {
+            col_of_rank[t] = rank_of[t];
+            dead[t] = (t >= nl);
+        }
+        nlive_s = nl;
+    }
+    __syncthreads();
+    const int nlive = nlive_s;
+    for (int t = nlive + warp; t < r; t += EIG_THREADS / 32) {
+        float2* w = W + col_of_rank[t] * EIG_RS;
+        float ss = 0.f;
+        for (int row = wl; row < r; row += 32) {
+            const float2 v = gauss2(977 + t, row, t);
+            w[row] = v;
+            ss = fmaf(v.x, v.x, fmaf(v.y, v.y, ss));
+        }
+        for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
+        const float inv = ss > 0.f ? rsqrtf(ss) : 0.f;
+        for (int row = wl; row < r; row += 32) w[row] = cscale(w[row], inv);
+    }
+    __syncthreads();
+    for (int t0 = nlive; t0 < r; t0 += EIG_CB) {
+        const int nb = min(EIG_CB, r - t0);
+        if (tid < EIG_CB) bdead[tid] = (tid < nb) ? 0 : 1;
+        __syncthreads();
+        ortho_block(t0, nb);
+    }
+    for (int t = tid; t < r; t += EIG_THREADS) {
+        const int j = col_of_rank[t];
+        rank_of[j] = t;
+        lam[t] = (t < nlive) ? nrm[j] : 0.0;
+    }
+    __syncthreads();
     for (int e = tid; e < r * r; e += EIG_THREADS) {
         int j = e / r, row = e % r;
         U[(long long)rank_of[j] * ldu + row] = W[j * EIG_RS + row];
