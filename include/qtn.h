@@ -126,9 +126,8 @@ long long qtn_launch_count(void);
  * launches of two kernel classes are bracketed by CUDA events on their stream
  * and their algorithmic FLOPs are accumulated on the device in the workspace:
  *   class 0: the complex GEMM kernel (8 M N K FLOPs per product);
- *   class 1: the shared-memory Jacobi eigensolver (16 r FLOPs per evaluated
- *            column pair, 24 r per rotation, 16 r^3 for the two Gram-Schmidt
- *            passes).
+ *   class 1: the shared-memory Jacobi eigensolver (8 r FLOPs per evaluated
+ *            column pair, 24 r per rotation, 8 r^3 for the re-orthonormalisation).
  * qtn_profile_read synchronises and returns the total device time (ms), the
  * launch count and the FLOP total of one class since qtn_profile(.., 1, ..). */
 qtn_status qtn_profile(void* ctx, int enable, void* ws, size_t ws_bytes);

@@ -141,7 +141,8 @@ cudaError_t launch_gemm(const GemmDesc& d, int max_m, int max_n, int max_k, cons
 
 // ------------------------------------------------------------------ one-sided Jacobi eigensolver
 constexpr int EIG_THREADS = 1024;
-constexpr int EIG_GL = 8;                       // lanes per column pair
+constexpr int EIG_GL = 16;                      // lanes per column pair: one half-warp reads 16 consecutive rows
+                                                // of a column, 128 bytes, conflict-free
 constexpr int EIG_GROUPS = EIG_THREADS / EIG_GL;
 constexpr int EIG_RS = EIG_MAX + 1;             // odd column stride: strided column reads hit distinct banks
 constexpr int EIG_CB = 16;                      // columns per block of the re-orthonormalisation
@@ -192,11 +193,24 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
 
     const int rr = r + (r & 1);
     const int grp = tid / EIG_GL, lane = tid % EIG_GL;
-    const unsigned gmask = 0xFFu << ((tid % 32) / EIG_GL * EIG_GL);
+    const unsigned gmask = ((1u << EIG_GL) - 1u) << ((tid % 32) / EIG_GL * EIG_GL);
+    // squared column norms, exact at the start of every sweep and carried through each rotation by
+    // |x'|^2 = |x|^2 - t |c|, |y'|^2 = |y|^2 + t |c|, so a pair needs only its inner product
+    __shared__ float cn2[EIG_MAX];
+    unsigned long long my_pairs = 0ull, my_rot = 0ull;
     int sweep = 0;
     bool converged = (r < 2);
     for (; sweep < max_sweeps && !converged; ++sweep) {
         if (tid == 0) rotated = 0;
+        for (int j = tid / 32; j < r; j += EIG_THREADS / 32) {
+            float s2 = 0.f;
+            for (int row = tid % 32; row < r; row += 32) {
+                const float2 x = W[j * EIG_RS + row];
+                s2 = fmaf(x.x, x.x, fmaf(x.y, x.y, s2));
+            }
+            for (int off = 16; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+            if (tid % 32 == 0) cn2[j] = s2;
+        }
         __syncthreads();
         for (int t = 0; t < rr - 1; ++t) {
             for (int k = grp; k < rr / 2; k += EIG_GROUPS) {
@@ -205,22 +219,28 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
                 if (i >= r || j >= r) continue;
                 float2* wi = W + i * EIG_RS;
                 float2* wj = W + j * EIG_RS;
-                float a = 0.f, b = 0.f, cr = 0.f, ci = 0.f;
-                for (int row = lane; row < r; row += EIG_GL) {
-                    float2 x = wi[row], y = wj[row];
-                    a = fmaf(x.x, x.x, fmaf(x.y, x.y, a));
-                    b = fmaf(y.x, y.x, fmaf(y.y, y.y, b));
-                    cr = fmaf(x.x, y.x, fmaf(x.y, y.y, cr));    // conj(x) * y
-                    ci = fmaf(x.x, y.y, fmaf(-x.y, y.x, ci));
+                float cr0 = 0.f, ci0 = 0.f, cr1 = 0.f, ci1 = 0.f;   // two chains for instruction-level overlap
+                int row = lane;
+                for (; row + EIG_GL < r; row += 2 * EIG_GL) {
+                    const float2 x0 = wi[row], y0 = wj[row], x1 = wi[row + EIG_GL], y1 = wj[row + EIG_GL];
+                    cr0 = fmaf(x0.x, y0.x, fmaf(x0.y, y0.y, cr0));    // conj(x) * y
+                    ci0 = fmaf(x0.x, y0.y, fmaf(-x0.y, y0.x, ci0));
+                    cr1 = fmaf(x1.x, y1.x, fmaf(x1.y, y1.y, cr1));
+                    ci1 = fmaf(x1.x, y1.y, fmaf(-x1.y, y1.x, ci1));
                 }
+                if (row < r) {
+                    const float2 x0 = wi[row], y0 = wj[row];
+                    cr0 = fmaf(x0.x, y0.x, fmaf(x0.y, y0.y, cr0));
+                    ci0 = fmaf(x0.x, y0.y, fmaf(-x0.y, y0.x, ci0));
+                }
+                float cr = cr0 + cr1, ci = ci0 + ci1;
 #pragma unroll
                 for (int off = EIG_GL / 2; off > 0; off >>= 1) {
-                    a += __shfl_xor_sync(gmask, a, off);
-                    b += __shfl_xor_sync(gmask, b, off);
                     cr += __shfl_xor_sync(gmask, cr, off);
                     ci += __shfl_xor_sync(gmask, ci, off);
                 }
-                if (lane == 0 && prof != nullptr) atomicAdd(&n_pairs, 1ull);
+                ++my_pairs;
+                const float a = cn2[i], b = cn2[j];
                 const float cabs = sqrtf(cr * cr + ci * ci);
                 // Columns of the scaled matrix whose norms are both below the FP32 resolution of G are
                 // round-off: rotating them never converges and they are orthonormalised afterwards.
@@ -229,25 +249,28 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
                 const float zeta = (b - a) / (2.f * cabs);
                 const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
                 const float cs = rsqrtf(fmaf(tt, tt, 1.f));
-                const float sn = tt * cs;
-                const float er = cr / cabs, ei = ci / cabs;
-                for (int row = lane; row < r; row += EIG_GL) {
-                    float2 x = wi[row], y = wj[row];
-                    // x' = cs x - sn conj(e) y ;  y' = sn e x + cs y
-                    float2 cey = make_float2(er * y.x + ei * y.y, er * y.y - ei * y.x);
-                    float2 ex = make_float2(er * x.x - ei * x.y, er * x.y + ei * x.x);
-                    wi[row] = make_float2(cs * x.x - sn * cey.x, cs * x.y - sn * cey.y);
-                    wj[row] = make_float2(sn * ex.x + cs * y.x, sn * ex.y + cs * y.y);
+                const float pr = tt * cs * cr / cabs, pi = tt * cs * ci / cabs;   // p = sin(theta) e
+                // x' = cs x - conj(p) y ;  y' = p x + cs y
+                for (int rw = lane; rw < r; rw += EIG_GL) {
+                    const float2 x = wi[rw], y = wj[rw];
+                    wi[rw] = make_float2(fmaf(cs, x.x, -fmaf(pr, y.x, pi * y.y)), fmaf(cs, x.y, -fmaf(pr, y.y, -pi * y.x)));
+                    wj[rw] = make_float2(fmaf(cs, y.x, fmaf(pr, x.x, -pi * x.y)), fmaf(cs, y.y, fmaf(pr, x.y, pi * x.x)));
                 }
                 if (lane == 0) {
+                    cn2[i] = fmaxf(a - tt * cabs, 0.f);
+                    cn2[j] = b + tt * cabs;
                     rotated = 1;
-                    if (prof != nullptr) atomicAdd(&n_rot, 1ull);
+                    ++my_rot;
                 }
             }
             __syncthreads();
         }
         converged = (rotated == 0);
         __syncthreads();
+    }
+    if (prof != nullptr && lane == 0 && (my_pairs | my_rot)) {
+        atomicAdd(&n_pairs, my_pairs);
+        atomicAdd(&n_rot, my_rot);
     }
     // eigenvalues = column norms (FP64 accumulation), eigenvectors = normalised columns
     for (int j = tid / 32; j < r; j += EIG_THREADS / 32) {
@@ -353,34 +376,35 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
                 if (wl == 0) Rb[c1 * EIG_CB + c2] = make_float2(sr, si);
             }
             __syncthreads();
-            // Cholesky factor (upper, row c of Rb), one warp; a pivot below the threshold marks the column
-            // dependent (first run: relative residual EIG_DEP0 of a unit column; second run: half of it)
+            // Cholesky factor (upper, row c of Rb), right-looking, one warp: the pivot is the diagonal of the
+            // updated trailing Gram and the trailing update is spread over the lanes.  A pivot below the
+            // threshold marks the column dependent (first run: relative residual EIG_DEP0 of a unit column;
+            // second run: half of it).
             if (warp == 0) {
                 const float thr2 = pass == 0 ? EIG_DEP0 * EIG_DEP0 : 0.25f;
                 for (int c = 0; c < nb; ++c) {
-                    float d = Rb[c * EIG_CB + c].x;
-                    for (int k = 0; k < c; ++k) {
-                        const float2 v = Rb[k * EIG_CB + c];
-                        d -= v.x * v.x + v.y * v.y;
-                    }
+                    const float d = Rb[c * EIG_CB + c].x;
                     const bool dc = bdead[c] || !(d > thr2);
-                    __syncwarp();                            // every lane has read the pivot row
+                    __syncwarp();
                     if (dc) {
                         if (wl >= c && wl < nb) Rb[c * EIG_CB + wl] = make_float2(0.f, 0.f);
                         if (wl == 0) bdead[c] = 1;
-                    } else {
-                        const float rcc = sqrtf(d), inv = 1.f / rcc;
-                        if (wl > c && wl < nb) {
-                            float2 v = Rb[c * EIG_CB + wl];
-                            for (int k = 0; k < c; ++k) {
-                                const float2 a = Rb[k * EIG_CB + c], b = Rb[k * EIG_CB + wl];   // conj(a) * b
-                                v.x -= a.x * b.x + a.y * b.y;
-                                v.y -= a.x * b.y - a.y * b.x;
-                            }
-                            Rb[c * EIG_CB + wl] = cscale(v, inv);
-                        }
                         __syncwarp();
-                        if (wl == 0) Rb[c * EIG_CB + c] = make_float2(rcc, 0.f);
+                        continue;
+                    }
+                    const float rcc = sqrtf(d), inv = 1.f / rcc;
+                    if (wl > c && wl < nb) Rb[c * EIG_CB + wl] = cscale(Rb[c * EIG_CB + wl], inv);
+                    if (wl == c) Rb[c * EIG_CB + c] = make_float2(rcc, 0.f);
+                    __syncwarp();
+                    const int mt = nb - c - 1;                // trailing block, upper triangle
+                    for (int p = wl; p < mt * mt; p += 32) {
+                        const int i2 = c + 1 + p / mt, i3 = c + 1 + p % mt;
+                        if (i3 < i2) continue;
+                        const float2 u = Rb[c * EIG_CB + i2], v = Rb[c * EIG_CB + i3];   // conj(u) * v
+                        float2 g = Rb[i2 * EIG_CB + i3];
+                        g.x -= u.x * v.x + u.y * v.y;
+                        g.y -= u.x * v.y - u.y * v.x;
+                        Rb[i2 * EIG_CB + i3] = g;
                     }
                     __syncwarp();
                 }
@@ -460,10 +484,10 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
     if (tid == 0) {
         atomicMax(&Rw[R_SWEEPS], sweep);
         if (!converged) atomicOr(&Rw[R_FLAGS], 1);
-        // algorithmic FLOPs: 16 per row for the three inner products of a pair, 24 per row for a rotation,
-        // 8 r^3 for the classical Gram-Schmidt pass (coefficients and updates, complex)
+        // algorithmic FLOPs: 8 per row for the inner product of a pair, 24 per row for a rotation,
+        // 8 r^3 for the re-orthonormalisation (projections and Cholesky QR, complex)
         if (prof != nullptr)
-            atomicAdd(prof, 16.0 * r * (double)n_pairs + 24.0 * r * (double)n_rot + 8.0 * (double)r * r * r);
+            atomicAdd(prof, 8.0 * r * (double)n_pairs + 24.0 * r * (double)n_rot + 8.0 * (double)r * r * r);
     }
 }
 
