@@ -228,6 +228,56 @@ qtn_status qtn_kron_interleave(void* ctx, const qtn_mps* x, const qtn_mps* y, qt
  * synchronises. */
 qtn_status qtn_add(void* ctx, const qtn_mps* a, const qtn_mps* b, qtn_mps* out);
 
+/* Batched Fresnel steps over many independent interleaved wavefronts (the
+ * data-parallel execution of Sec. VI.A over a batch; the paper treats one field
+ * at a time).  Item i is advanced on its own context ctxs[i] (its own stream,
+ * not the legacy default stream) with its own workspace ws[i] and operators
+ * qft[i], qft_dagger[i], phase[i] (arrays of count; items may differ in n and
+ * chi).  qtn_batch_create records n_steps steps of every item into one CUDA
+ * graph per item without running them; qtn_batch_launch(batch, k) launches
+ * every item's graph k times, so the items run concurrently across the GPU.
+ * The items, operators and workspaces must stay allocated and unmoved while
+ * the batch exists; profiling must be off; statistics are not collected (use
+ * qtn_norm2 / qtn_overlap afterwards).  Each item should be in a canonical
+ * form before creation (as qtn_encode and qtn_truncate leave it). */
+qtn_status qtn_batch_create(int count, void* const* ctxs, qtn_mps* items, const qtn_mpo* qft,
+                            const qtn_mpo* qft_dagger, const qtn_mpo* phase, int n_steps, qtn_trunc trunc,
+                            void* const* ws, const size_t* ws_bytes, void** batch);
+qtn_status qtn_batch_launch(void* batch, int repeats);
+qtn_status qtn_batch_destroy(void* batch);
+
+/* Elementwise (Hadamard) product of two MPS in the same site basis (Sec. V,
+ * Eq. psf_eq: the local product of physical legs, O(d chi^3) per site):
+ * out[s] = a[s] * b[s] (conj(b[s]) when conj_b != 0); bonds multiply.
+ * out: same n_sites and d, chi_cap >= bond_a * bond_b at every bond
+ * (QTN_ERR_CAPACITY otherwise); must not alias a or b.  Result canon NONE;
+ * compress with qtn_truncate.  The call synchronises (it checks the bonds). */
+qtn_status qtn_hadamard(void* ctx, const qtn_mps* a, const qtn_mps* b, int conj_b, qtn_mps* out);
+
+/* psi <- truncate(psi (.) b): the elementwise product with the MPS b (conj(b)
+ * when conj_b != 0) applied by zip-up, i.e. b acts as an operator that is
+ * diagonal in the site index, with SVD truncation by `trunc` (the product of
+ * Sec. V, Eq. psf_eq, without forming the chi_psi * chi_b intermediate).  Both
+ * states interleaved (d = 4) with the same n_sites; b must not alias psi; the
+ * workspace must allow MPO bonds up to b's largest bond.  psi is brought to a
+ * canonical form first when it has none.  The call reads b's bonds on the host. */
+qtn_status qtn_hadamard_zipup(void* ctx, const qtn_mps* b, int conj_b, qtn_mps* psi, qtn_trunc trunc,
+                              qtn_stats* stats, void* ws, size_t ws_bytes);
+
+/* Derivative of the overlap <a|b> = sum_s conj(a[s]) b[s] with respect to the
+ * conjugate of every site tensor of a (left and right transfer-matrix
+ * environments, FP64 accumulation): grad[p][k, s, m] = sum over all other
+ * site indices of b[s] conj(L_p[k]) conj(R_p[m]), L_p/R_p the products of a's
+ * sites left/right of p.  This is the chain rule from a field gradient to the
+ * site tensors that parametrise it.  grad: device complex64 with a's site
+ * layout [N][chi_cap_a][d][chi_cap_a].  The environments must fit the
+ * workspace (N chi_cap_a chi_cap_b <= its Gram capacity). */
+qtn_status qtn_overlap_grad(void* ctx, const qtn_mps* a, const qtn_mps* b, void* grad, void* ws, size_t ws_bytes);
+
+/* psi <- (re + i im) psi, applied to the site that carries the norm (the last
+ * site of a left-canonical state, the first otherwise); canon unchanged. */
+qtn_status qtn_scale(void* ctx, qtn_mps* psi, double re, double im);
+
 /* Zip-up MPO x MPS application with SVD truncation (Sec. V, Fig. fig_mpo).
  * The per-axis MPO W acts on axis `axis` (0 = x, 1 = y) of psi:
  *   INTERLEAVED: on the x (high) or y (low) bit of every d = 4 site;

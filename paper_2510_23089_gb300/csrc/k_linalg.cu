@@ -545,6 +545,7 @@ void count_launch(int cls, cudaStream_t s, bool before) {
 }
 
 long long launch_total() { return g_launches; }
+void add_launches(long long n) { g_launches += n; }
 
 void prof_begin(bool on, double* ledger) {
     g_prof_on = on;

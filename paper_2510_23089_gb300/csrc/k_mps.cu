@@ -76,6 +76,16 @@ __global__ void k_stage2(const float2* __restrict__ P, float2* __restrict__ T, c
             T[e] = P[(long long)x * dn + sp * chiR + k];
             continue;
         }
+        if (axis >= 2) {   // elementwise product with an MPS (the "MPO" is diagonal in the whole site index)
+            float2 acc = make_float2(0.f, 0.f);
+            for (int a = 0; a < wl; ++a) {
+                float2 w = mirror ? Wc[((long long)b * d + sp) * wcap + a] : Wc[((long long)a * d + sp) * wcap + b];
+                if (axis == 3) w.y = -w.y;
+                cfma(acc, P[(long long)(x * wl + a) * dn + sp * chiR + k], w);
+            }
+            T[e] = acc;
+            continue;
+        }
         int t, so;
         if (d == 2) { t = sp; so = 0; }
         else if (axis == 0) { t = sp >> 1; so = sp & 1; }
@@ -662,6 +672,60 @@ __global__ void k_transfer_step(const double2* __restrict__ E, int lde, const fl
     }
 }
 
+// Right transfer-matrix step of <a|b>: E'[k, l] = sum_{i, j, s} conj(A[k, s, i]) B[l, s, j] E[i, j], FP64 E.
+// One block per output row k (bra bond); threads over l (ket bond).
+__global__ void k_transfer_right(const double2* __restrict__ E, int lde, const float2* __restrict__ A, int acap,
+                                 int abl, int abr, const float2* __restrict__ B, int bcap, int bbl, int bbr, int d,
+                                 double2* __restrict__ En, int ldn) {
+    const int k = blockIdx.x;
+    if (k >= abl) return;
+    for (int l = threadIdx.x; l < bbl; l += blockDim.x) {
+        double re = 0.0, im = 0.0;
+        for (int s = 0; s < d; ++s) {
+            for (int i = 0; i < abr; ++i) {
+                // t_i = sum_j B[l, s, j] E[i, j]
+                double tr = 0.0, ti = 0.0;
+                for (int j = 0; j < bbr; ++j) {
+                    const float2 b = B[((long long)l * d + s) * bcap + j];
+                    const double2 e = E[(long long)i * lde + j];
+                    tr += (double)b.x * e.x - (double)b.y * e.y;
+                    ti += (double)b.x * e.y + (double)b.y * e.x;
+                }
+                const float2 a = A[((long long)k * d + s) * acap + i];   // conj(a) * t
+                re += (double)a.x * tr + (double)a.y * ti;
+                im += (double)a.x * ti - (double)a.y * tr;
+            }
+        }
+        En[(long long)k * ldn + l] = make_double2(re, im);
+    }
+}
+
+// Derivative of <a|b> with respect to conj(a_p): H[k, s, m] = sum_{i, j} EL[k, i] B_p[i, s, j] ER[m, j]
+// (EL: left environment of site p, bra index first; ER: right environment).  One block per k.
+__global__ void k_env_grad(const double2* __restrict__ EL, int ldl, const double2* __restrict__ ER, int ldr,
+                           const float2* __restrict__ B, int bcap, int bbl, int bbr, int abl, int abr, int d,
+                           float2* __restrict__ H, int hcap) {
+    const int k = blockIdx.x;
+    if (k >= abl) return;
+    for (int e = threadIdx.x; e < d * abr; e += blockDim.x) {
+        const int s = e / abr, m = e % abr;
+        double re = 0.0, im = 0.0;
+        for (int i = 0; i < bbl; ++i) {
+            const double2 el = EL[(long long)k * ldl + i];
+            double tr = 0.0, ti = 0.0;   // sum_j B[i, s, j] ER[m, j]
+            for (int j = 0; j < bbr; ++j) {
+                const float2 b = B[((long long)i * d + s) * bcap + j];
+                const double2 er = ER[(long long)m * ldr + j];
+                tr += (double)b.x * er.x - (double)b.y * er.y;
+                ti += (double)b.x * er.y + (double)b.y * er.x;
+            }
+            re += el.x * tr - el.y * ti;
+            im += el.x * ti + el.y * tr;
+        }
+        H[((long long)k * d + s) * hcap + m] = make_float2((float)re, (float)im);
+    }
+}
+
 // ------------------------------------------------------------------ state construction
 
 // Interleaved d = 4 MPS of f(x) g(y) from 1-D MPS of f and g (Sec. III: site p holds mu_p = 2 x_p + y_p):
@@ -686,6 +750,43 @@ __global__ void k_kron_interleave(const float2* __restrict__ X, const int* __res
     if (threadIdx.x == 0) {
         ob[p] = ol;
         if (p == n - 1) ob[n] = orr;
+    }
+}
+
+// Elementwise (Hadamard) product of two MPS in the same site basis: O_p[(a, b), s, (a', b')] =
+// A_p[a, s, a'] B_p[b, s, b'] (B conjugated when conj_b), bonds multiply.  One block per site.
+__global__ void k_hadamard(const float2* __restrict__ A, const int* __restrict__ ab, int acap,
+                           const float2* __restrict__ B, const int* __restrict__ bb, int bcap, int conj_b,
+                           float2* __restrict__ O, int* __restrict__ ob, int ocap, int N, int d) {
+    const int p = blockIdx.x;
+    if (p >= N) return;
+    const int al = ab[p], ar = ab[p + 1], bl = bb[p], br = bb[p + 1];
+    const int ol = al * bl, orr = ar * br;
+    const float2* a = A + (long long)p * acap * d * acap;
+    const float2* b = B + (long long)p * bcap * d * bcap;
+    float2* o = O + (long long)p * ocap * d * ocap;
+    for (int e = threadIdx.x; e < ol * d * orr; e += blockDim.x) {
+        const int l = e / (d * orr), s = (e / orr) % d, r = e % orr;
+        const int l1 = l / bl, l2 = l % bl, r1 = r / br, r2 = r % br;
+        float2 y = b[((long long)l2 * d + s) * bcap + r2];
+        if (conj_b) y.y = -y.y;
+        o[((long long)l * d + s) * ocap + r] = cmul(a[((long long)l1 * d + s) * acap + r1], y);
+    }
+    if (threadIdx.x == 0) {
+        ob[p] = ol;
+        if (p == N - 1) ob[N] = orr;
+    }
+}
+
+// psi <- (re + i im) psi, applied to the site that holds the norm (site 0 unless the state is
+// left-canonical, then site N-1).
+__global__ void k_scale_site(float2* __restrict__ site, int cap, int d, const int* __restrict__ bond, int q, float re,
+                             float im) {
+    const int l = bond[q], r = bond[q + 1];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < l * d * r; e += gridDim.x * blockDim.x) {
+        const int i = e / (d * r), s = (e / r) % d, j = e % r;
+        float2* v = site + ((long long)i * d + s) * cap + j;
+        *v = cmul(*v, make_float2(re, im));
     }
 }
 

@@ -33,6 +33,9 @@ __global__ void k_kron_interleave(const float2*, const int*, int, const float2*,
                                   int);
 __global__ void k_direct_sum(const float2*, const int*, int, const float2*, const int*, int, float2*, int*, int, int,
                              int);
+__global__ void k_hadamard(const float2*, const int*, int, const float2*, const int*, int, int, float2*, int*, int, int,
+                           int);
+__global__ void k_scale_site(float2*, int, int, const int*, int, float, float);
 constexpr int CGS_MAXM_ALL = 1024;
 __global__ void k_row_weights(const float2*, Dim, Dim, Dim, double*, const int*);
 __global__ void k_select(const double*, Dim, int, double, int, int, int*, int*, double*);
@@ -50,6 +53,10 @@ __global__ void k_phase_vector(float2*, int, double, int);
 __global__ void k_diag_mpo(const float2*, int, const int*, float2*, int, int*, int);
 __global__ void k_mpo_dagger(const float2*, const int*, int, float2*, int*, int, int);
 __global__ void k_amplitudes(const float2*, const int*, int, int, int, const int*, int, float2*, float2*);
+__global__ void k_transfer_right(const double2*, int, const float2*, int, int, int, const float2*, int, int, int, int,
+                                 double2*, int);
+__global__ void k_env_grad(const double2*, int, const double2*, int, const float2*, int, int, int, int, int, int,
+                           float2*, int);
 __global__ void k_transfer_step(const double2*, int, const float2*, int, int, int, const float2*, int, int, int, int,
                                 double2*);
 
@@ -162,6 +169,7 @@ static float2* ws_mtmp(void* base, const WsLayout& L) { return (float2*)((char*)
     } while (0)
 
 long long launch_total();
+void add_launches(long long n);
 void prof_begin(bool on, double* ledger);
 void prof_read(int cls, double* ms, long long* launches);
 
@@ -678,14 +686,16 @@ qtn_status qtn_encode(void* ctx, const void* dense, int n, qtn_layout layout, qt
 }
 
 // Internal: zip-up application without resetting the statistics.
-static qtn_status apply_inner(qtn_context* x, Ws& w, const qtn_mpo* W, int axis, qtn_mps* psi, const qtn_trunc& tr) {
+static qtn_status apply_inner(qtn_context* x, Ws& w, const qtn_mpo* W, int axis, qtn_mps* psi, const qtn_trunc& tr,
+                              bool diag = false) {
     const int d = psi->d, N = psi->n_sites;
     int moff = 0, mn = N;
     if (W) {
         mn = W->n_sites;
         if (d == 4) {
             if (N != mn) return QTN_ERR_SHAPE;
-            if (axis != 0 && axis != 1) return QTN_ERR_ARG;
+            // axis 2/3: W is an MPS viewed as a diagonal operator (elementwise product, conjugated for 3)
+            if (diag ? (axis != 2 && axis != 3) : (axis != 0 && axis != 1)) return QTN_ERR_ARG;
         } else if (N == mn) {
             axis = 0;
         } else if (N == 2 * mn) {
@@ -918,6 +928,109 @@ qtn_status qtn_add(void* ctx, const qtn_mps* a, const qtn_mps* b, qtn_mps* out) 
     return QTN_OK;
 }
 
+qtn_status qtn_hadamard(void* ctx, const qtn_mps* a, const qtn_mps* b, int conj_b, qtn_mps* out) {
+    if (!ctx || !a || !b || !out) return QTN_ERR_ARG;
+    const int N = a->n_sites, d = a->d;
+    if (b->n_sites != N || out->n_sites != N || b->d != d || out->d != d) return QTN_ERR_SHAPE;
+    if (out->sites == a->sites || out->sites == b->sites) return QTN_ERR_ARG;
+    qtn_context* c = (qtn_context*)ctx;
+    std::vector<int> ha(N + 1), hb(N + 1);
+    CK(cudaMemcpyAsync(ha.data(), a->bond, (N + 1) * sizeof(int), cudaMemcpyDeviceToHost, c->c.stream));
+    CK(cudaMemcpyAsync(hb.data(), b->bond, (N + 1) * sizeof(int), cudaMemcpyDeviceToHost, c->c.stream));
+    CK(cudaStreamSynchronize(c->c.stream));
+    for (int p = 0; p <= N; ++p)
+        if ((long long)ha[p] * hb[p] > out->chi_cap) return QTN_ERR_CAPACITY;
+    k_hadamard<<<N, 256, 0, c->c.stream>>>((const float2*)a->sites, a->bond, a->chi_cap, (const float2*)b->sites,
+                                           b->bond, b->chi_cap, conj_b ? 1 : 0, (float2*)out->sites, out->bond,
+                                           out->chi_cap, N, d);
+    CKL();
+    out->canon = QTN_CANON_NONE;
+    return QTN_OK;
+}
+
+qtn_status qtn_hadamard_zipup(void* ctx, const qtn_mps* b, int conj_b, qtn_mps* psi, qtn_trunc trunc,
+                              qtn_stats* stats, void* ws, size_t ws_bytes) {
+    if (!ctx || !b || !psi) return QTN_ERR_ARG;
+    if (b->d != 4 || psi->d != 4 || b->n_sites != psi->n_sites) return QTN_ERR_SHAPE;
+    if (b->sites == psi->sites) return QTN_ERR_ARG;
+    qtn_context* x = (qtn_context*)ctx;
+    Ws w;
+    qtn_status st = bind_ws(x, ws, ws_bytes, w);
+    if (st) return st;
+    const int N = b->n_sites;
+    std::vector<int> hb(N + 1);
+    CK(cudaMemcpyAsync(hb.data(), b->bond, (N + 1) * sizeof(int), cudaMemcpyDeviceToHost, x->c.stream));
+    CK(cudaStreamSynchronize(x->c.stream));
+    int wmax = 1;
+    for (int p = 0; p <= N; ++p) wmax = std::max(wmax, hb[p]);
+    // the MPS b seen as a diagonal operator: its sites have the stride of an MPO core when d = 4
+    qtn_mpo view{N, b->chi_cap, wmax, b->bond, b->sites};
+    k_reset_stats<<<1, 1, 0, x->c.stream>>>(w.R, w.ledger);
+    CKL();
+    st = apply_inner(x, w, &view, conj_b ? 3 : 2, psi, trunc, true);
+    if (st) return st;
+    return fill_stats(&x->c, w, stats);
+}
+
+qtn_status qtn_overlap_grad(void* ctx, const qtn_mps* a, const qtn_mps* b, void* grad, void* ws, size_t ws_bytes) {
+    if (!ctx || !a || !b || !grad || a->n_sites != b->n_sites || a->d != b->d) return QTN_ERR_ARG;
+    qtn_context* x = (qtn_context*)ctx;
+    Ws w;
+    qtn_status st = bind_ws(x, ws, ws_bytes, w);
+    if (st) return st;
+    cudaStream_t s = x->c.stream;
+    const int N = a->n_sites, d = a->d;
+    const int gld = std::max(w.L.m_cap, w.L.p_cap);
+    // environments, bra index first: EL[p] (sites < p) in G64, ER[p] (sites > p) in S64, stride ea x eb
+    const int ea = a->chi_cap, eb = b->chi_cap;
+    const size_t env = (size_t)ea * eb;
+    if (env * N > (size_t)gld * gld) return QTN_ERR_WORKSPACE;
+    std::vector<int> ba(N + 1), bb(N + 1);
+    CK(cudaMemcpyAsync(ba.data(), a->bond, (N + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(bb.data(), b->bond, (N + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double2* EL = w.G64;
+    double2* ER = w.S64;
+    const double2 one = make_double2(1.0, 0.0);
+    CK(cudaMemcpyAsync(EL, &one, sizeof(double2), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ER + (size_t)(N - 1) * env, &one, sizeof(double2), cudaMemcpyHostToDevice, s));
+    const size_t sa = (size_t)ea * d * ea, sb = (size_t)eb * d * eb;
+    for (int p = 0; p + 1 < N; ++p) {
+        const float2* A = (const float2*)a->sites + p * sa;
+        const float2* B = (const float2*)b->sites + p * sb;
+        k_transfer_step<<<ba[p + 1], 128, 0, s>>>(EL + p * env, eb, A, ea, ba[p], ba[p + 1], B, eb, bb[p], bb[p + 1],
+                                                  d, EL + (p + 1) * env);
+        CKL();
+    }
+    for (int p = N - 1; p > 0; --p) {
+        const float2* A = (const float2*)a->sites + p * sa;
+        const float2* B = (const float2*)b->sites + p * sb;
+        k_transfer_right<<<ba[p], 128, 0, s>>>(ER + p * env, eb, A, ea, ba[p], ba[p + 1], B, eb, bb[p], bb[p + 1], d,
+                                               ER + (p - 1) * env, eb);
+        CKL();
+    }
+    CK(cudaMemsetAsync(grad, 0, (size_t)N * sa * sizeof(float2), s));
+    for (int p = 0; p < N; ++p) {
+        const float2* B = (const float2*)b->sites + p * sb;
+        k_env_grad<<<ba[p], 256, 0, s>>>(EL + p * env, eb, ER + p * env, eb, B, eb, bb[p], bb[p + 1], ba[p], ba[p + 1],
+                                         d, (float2*)grad + p * sa, ea);
+        CKL();
+    }
+    return QTN_OK;
+}
+
+qtn_status qtn_scale(void* ctx, qtn_mps* psi, double re, double im) {
+    if (!ctx || !psi || psi->n_sites < 1) return QTN_ERR_ARG;
+    qtn_context* c = (qtn_context*)ctx;
+    const int N = psi->n_sites, cap = psi->chi_cap, d = psi->d;
+    const int q = (psi->canon == QTN_CANON_LEFT) ? N - 1 : 0;
+    float2* site = (float2*)psi->sites + (size_t)q * cap * d * cap;
+    k_scale_site<<<grid_for((long long)cap * d * cap, 256, c->c.sm_count), 256, 0, c->c.stream>>>(
+        site, cap, d, psi->bond, q, (float)re, (float)im);
+    CKL();
+    return QTN_OK;
+}
+
 qtn_status qtn_mpo_dagger(void* ctx, const qtn_mpo* in, qtn_mpo* out) {
     if (!ctx || !in || !out || in->n_sites != out->n_sites || out->w_cap < in->w_max) return QTN_ERR_ARG;
     if (in->sites == out->sites) return QTN_ERR_ARG;
@@ -1040,6 +1153,83 @@ qtn_status qtn_amplitudes(void* ctx, const qtn_mps* psi, const int* digits, int 
                                                          (float2*)out + s0, w.X0);
         CKL();
     }
+    return QTN_OK;
+}
+
+// ---------------------------------------------------------------------------- batched steps in CUDA graphs
+
+}  // extern "C"
+
+struct qtn_batch {
+    std::vector<cudaGraphExec_t> exec;
+    std::vector<cudaStream_t> stream;
+    long long kernels_per_launch = 0;
+};
+
+extern "C" {
+
+qtn_status qtn_batch_create(int count, void* const* ctxs, qtn_mps* items, const qtn_mpo* qft, const qtn_mpo* qft_dagger,
+                            const qtn_mpo* phase, int n_steps, qtn_trunc trunc, void* const* ws,
+                            const size_t* ws_bytes, void** batch) {
+    if (count < 1 || !ctxs || !items || !qft || !qft_dagger || !phase || !ws || !ws_bytes || !batch || n_steps < 1)
+        return QTN_ERR_ARG;
+    qtn_batch* b = new qtn_batch;
+    qtn_status result = QTN_OK;
+    const long long launches0 = launch_total();
+    for (int i = 0; i < count && result == QTN_OK; ++i) {
+        qtn_context* x = (qtn_context*)ctxs[i];
+        if (!x || x->c.stream == nullptr) { result = QTN_ERR_ARG; break; }   // the legacy stream cannot be captured
+        Ws w;
+        if ((result = bind_ws(x, ws[i], ws_bytes[i], w))) break;
+        qtn_mps* psi = items + i;
+        const int canon0 = psi->canon;
+        const int naxes = 2;
+        const qtn_mpo* ops[3] = {qft + i, phase + i, qft_dagger + i};
+        cudaStream_t s = x->c.stream;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) { result = QTN_ERR_CUDA; break; }
+        qtn_status st = QTN_OK;
+        k_reset_stats<<<1, 1, 0, s>>>(w.R, w.ledger);
+        count_launch(PROF_OTHER, 0, false);
+        for (int step = 0; step < n_steps && st == QTN_OK; ++step)
+            for (int o = 0; o < 3 && st == QTN_OK; ++o)
+                for (int ax = 0; ax < naxes && st == QTN_OK; ++ax) st = apply_inner(x, w, ops[o], ax, psi, trunc);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(s, &g);
+        // capturing executed nothing: the item is unchanged, so is its canonical form
+        psi->canon = canon0;
+        if (st) { result = st; if (g) cudaGraphDestroy(g); break; }
+        if (ec != cudaSuccess || !g) { result = QTN_ERR_CUDA; break; }
+        cudaGraphExec_t e = nullptr;
+        const cudaError_t ei = cudaGraphInstantiate(&e, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) { result = QTN_ERR_CUDA; break; }
+        b->exec.push_back(e);
+        b->stream.push_back(s);
+    }
+    if (result != QTN_OK) {
+        for (auto e : b->exec) cudaGraphExecDestroy(e);
+        delete b;
+        return result;
+    }
+    b->kernels_per_launch = launch_total() - launches0;
+    *batch = b;
+    return QTN_OK;
+}
+
+qtn_status qtn_batch_launch(void* batch, int repeats) {
+    if (!batch || repeats < 0) return QTN_ERR_ARG;
+    qtn_batch* b = (qtn_batch*)batch;
+    for (int rep = 0; rep < repeats; ++rep)
+        for (size_t i = 0; i < b->exec.size(); ++i) CK(cudaGraphLaunch(b->exec[i], b->stream[i]));
+    add_launches(b->kernels_per_launch * repeats);
+    return QTN_OK;
+}
+
+qtn_status qtn_batch_destroy(void* batch) {
+    if (!batch) return QTN_OK;
+    qtn_batch* b = (qtn_batch*)batch;
+    for (auto e : b->exec) cudaGraphExecDestroy(e);
+    delete b;
     return QTN_OK;
 }
 

@@ -34,6 +34,8 @@ EXPORTS = (
     "qtn_encode", "qtn_build_qft_mpo", "qtn_build_phase_mpo", "qtn_mpo_dagger", "qtn_apply_mpo", "qtn_truncate",
     "qtn_fresnel_step", "qtn_to_dense", "qtn_norm2", "qtn_overlap", "qtn_amplitudes", "qtn_tsvd",
     "qtn_kron_interleave", "qtn_add", "qtn_launch_count", "qtn_profile", "qtn_profile_read", "qtn_tsvd_noalloc",
+    "qtn_hadamard", "qtn_scale", "qtn_hadamard_zipup", "qtn_overlap_grad",
+    "qtn_batch_create", "qtn_batch_launch", "qtn_batch_destroy",
 )
 
 
@@ -95,6 +97,14 @@ def load_library(path: str = LIB_PATH):
         "qtn_tsvd_noalloc": [P, I, I, tr, P, P, I, ctypes.POINTER(I), st, P],
         "qtn_kron_interleave": [P, mp, mp, mp],
         "qtn_add": [P, mp, mp, mp],
+        "qtn_hadamard": [P, mp, mp, I, mp],
+        "qtn_scale": [P, mp, D, D],
+        "qtn_hadamard_zipup": [P, mp, I, mp, tr, st, P, S],
+        "qtn_overlap_grad": [P, mp, mp, P, P, S],
+        "qtn_batch_create": [I, ctypes.POINTER(P), mp, op, op, op, I, tr, ctypes.POINTER(P), ctypes.POINTER(S),
+                             ctypes.POINTER(P)],
+        "qtn_batch_launch": [P, I],
+        "qtn_batch_destroy": [P],
         "qtn_profile": [P, I, P, S],
         "qtn_profile_read": [P, I, ctypes.POINTER(D), ctypes.POINTER(LL), ctypes.POINTER(D), P, S],
     }
@@ -346,6 +356,31 @@ class Engine:
                "qtn_kron_interleave")
         return out
 
+    def hadamard(self, a: MPS, b: MPS, out: MPS, conj_b: bool = False) -> MPS:
+        _check(self.lib.qtn_hadamard(self.ctx, ctypes.byref(a.c), ctypes.byref(b.c), int(conj_b), ctypes.byref(out.c)),
+               "qtn_hadamard")
+        return out
+
+    def hadamard_zipup(self, b: MPS, psi: MPS, chi_max: int, cutoff: float, conj_b: bool = False,
+                       stats: bool = True):
+        """psi <- truncate(psi (.) b) by zip-up (b conjugated when conj_b)."""
+        st = c_stats()
+        _check(self.lib.qtn_hadamard_zipup(self.ctx, ctypes.byref(b.c), int(conj_b), ctypes.byref(psi.c),
+                                           self.trunc(chi_max, cutoff), ctypes.byref(st) if stats else None,
+                                           *self._ws()), "qtn_hadamard_zipup")
+        return _stats(st) if stats else None
+
+    def overlap_grad(self, a: MPS, b: MPS) -> torch.Tensor:
+        """d<a|b>/d conj(a's site tensors), same layout as a.sites."""
+        g = torch.empty_like(a.sites)
+        _check(self.lib.qtn_overlap_grad(self.ctx, ctypes.byref(a.c), ctypes.byref(b.c), ctypes.c_void_p(g.data_ptr()),
+                                         *self._ws()), "qtn_overlap_grad")
+        return g
+
+    def scale(self, psi: MPS, z: complex) -> MPS:
+        _check(self.lib.qtn_scale(self.ctx, ctypes.byref(psi.c), float(z.real), float(z.imag)), "qtn_scale")
+        return psi
+
     def add(self, a: MPS, b: MPS, out: MPS) -> MPS:
         _check(self.lib.qtn_add(self.ctx, ctypes.byref(a.c), ctypes.byref(b.c), ctypes.byref(out.c)), "qtn_add")
         return out
@@ -370,3 +405,40 @@ class Engine:
                                        digits.shape[0], ctypes.c_void_p(out.data_ptr()), *self._ws()),
                "qtn_amplitudes")
         return out
+
+
+class Batch:
+    """Fresnel steps of many independent interleaved items recorded as one CUDA graph per item
+    (qtn_batch_create) and launched together (qtn_batch_launch): item i runs on engines[i]'s stream with
+    engines[i]'s workspace and operators (Qs[i], Qds[i], Ds[i])."""
+
+    def __init__(self, engines, items, Qs, Qds, Ds, n_steps: int, chi_max: int, cutoff: float, prec: str = "fp32"):
+        lib = load_library()
+        self.lib, self.count = lib, len(items)
+        self._keep = (engines, items, Qs, Qds, Ds)
+        n = self.count
+        ctxs = (ctypes.c_void_p * n)(*[e.ctx.value for e in engines])
+        its = (c_mps * n)(*[it.c for it in items])
+        qa = (c_mpo * n)(*[q.c for q in Qs])
+        qda = (c_mpo * n)(*[q.c for q in Qds])
+        da = (c_mpo * n)(*[q.c for q in Ds])
+        wss = (ctypes.c_void_p * n)(*[e.ws.data_ptr() for e in engines])
+        wsb = (ctypes.c_size_t * n)(*[e.ws_bytes for e in engines])
+        h = ctypes.c_void_p()
+        _check(lib.qtn_batch_create(n, ctxs, its, qa, qda, da, n_steps, Engine.trunc(chi_max, cutoff, prec), wss, wsb,
+                                    ctypes.byref(h)), "qtn_batch_create")
+        self.handle = h
+
+    def launch(self, repeats: int = 1):
+        _check(self.lib.qtn_batch_launch(self.handle, repeats), "qtn_batch_launch")
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            self.lib.qtn_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -357,3 +357,28 @@ def test_c1_image_qft_against_brute_force_dft():
     err = np.linalg.norm(got - ref_br)
     assert err <= np.sqrt(sum(eps)) + 1e-6 * np.linalg.norm(img)
     assert max(OS.bonds(sites)) <= 16
+
+
+# ----------------------------------------------------------------------------- intensity loss and its adjoint
+
+def test_intensity_loss_gradient_matches_finite_differences():
+    # central differences of the dense loss in the real and imaginary part of single mask values: they pin
+    # the conjugate-Wirtinger gradient G (dL = 2 Re conj(G) dM) without using its formula
+    from oracle import optics as OO
+    rng = np.random.default_rng(61)
+    n = 3
+    L = 1 << n
+    E = rng.standard_normal((L, L)) + 1j * rng.standard_normal((L, L))
+    M = np.exp(1j * 0.3 * rng.standard_normal((L, L)))
+    It = rng.uniform(0, 2, size=(L, L))
+    c = 0.7
+    G = OO.intensity_loss_grad_dense(E, M, It, c)
+    h = 1e-6
+    for (i, j) in [(0, 0), (3, 5), (7, 2)]:
+        for unit in (1.0, 1j):
+            Mp, Mm = M.copy(), M.copy()
+            Mp[i, j] += h * unit
+            Mm[i, j] -= h * unit
+            fd = (OO.intensity_loss_dense(E, Mp, It, c) - OO.intensity_loss_dense(E, Mm, It, c)) / (2 * h)
+            pred = 2 * np.real(np.conj(G[i, j]) * unit)
+            assert abs(fd - pred) <= 1e-6 * max(1.0, abs(pred))
