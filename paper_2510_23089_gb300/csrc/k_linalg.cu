@@ -297,9 +297,10 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
     __syncthreads();
     // Re-orthonormalise the columns in descending-eigenvalue order: Jacobi leaves the directions below the
     // FP32 resolution of G non-orthogonal, and the new site must be an isometry.  Blocks of EIG_CB unit
-    // columns are projected on the finished columns and orthonormalised internally by Cholesky QR, twice
-    // (the second run restores what cancellation took from the first).  A column whose residual falls below
-    // EIG_DEP0 in the first run, or loses half of itself in the second, is numerically dependent: it is set
+    // columns are projected on the finished columns and orthonormalised internally by Cholesky QR; a second
+    // run restores what cancellation took from the first, when some column lost more than 30 % of itself.
+    // A column whose residual falls below EIG_DEP0 in the first run, or loses half of itself in the second,
+    // is numerically dependent: it is set
     // aside and replaced at the end by a pseudo-random vector orthonormalised the same way, so the basis
     // stays complete and no weight of the factorised matrix is lost.
     __shared__ int col_of_rank[EIG_MAX];
@@ -309,6 +310,7 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
     __shared__ float2 Rb[EIG_CB * EIG_CB];           // Gram of the block, overwritten by its Cholesky factor
     __shared__ unsigned char bdead[EIG_CB];
     __shared__ int nlive_s;
+    __shared__ int again_s;                           // the block needs its second run
     const int warp = tid / 32, wl = tid % 32;
     for (int j = tid; j < r; j += EIG_THREADS) {
         col_of_rank[rank_of[j]] = j;
@@ -382,9 +384,11 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
             // second run: half of it).
             if (warp == 0) {
                 const float thr2 = pass == 0 ? EIG_DEP0 * EIG_DEP0 : 0.25f;
+                bool heavy = false;
                 for (int c = 0; c < nb; ++c) {
                     const float d = Rb[c * EIG_CB + c].x;
                     const bool dc = bdead[c] || !(d > thr2);
+                    heavy = heavy || (!dc && d < 0.5f);   // a live column lost more than 30 % of its norm
                     __syncwarp();
                     if (dc) {
                         if (wl >= c && wl < nb) Rb[c * EIG_CB + wl] = make_float2(0.f, 0.f);
@@ -408,6 +412,7 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
                     }
                     __syncwarp();
                 }
+                if (wl == 0) again_s = heavy ? 1 : 0;
             }
             __syncthreads();
             // block <- block R^{-1} by forward substitution in place, one row per thread (dependent columns
@@ -425,6 +430,9 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
                 }
             }
             __syncthreads();
+            // without cancellation in the first run the block is orthonormal to working precision already
+            // (Cholesky QR of a well-conditioned block); the second run is for blocks that lost digits
+            if (pass == 0 && !again_s) break;
         }
     };
     for (int t0 = 0; t0 < r; t0 += EIG_CB) {
