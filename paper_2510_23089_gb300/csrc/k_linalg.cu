@@ -8,7 +8,8 @@
 //    positive semidefinite r x r matrix G held in shared memory (r <= 160).
 //    Columns converge to G V = U diag(lambda); normalised columns are the
 //    eigenvectors and their norms the eigenvalues.  Disjoint column pairs of a
-//    round-robin round are processed by 8-lane groups with shuffle reductions.
+//    round-robin round are processed by 16-lane groups with shuffle reductions;
+//    pairs whose columns have not moved since their last comparison are skipped.
 //  * k_select: the truncation rule on the sorted spectrum (FP64 bookkeeping).
 #include <math.h>
 #include <stdlib.h>
@@ -141,9 +142,6 @@ cudaError_t launch_gemm(const GemmDesc& d, int max_m, int max_n, int max_k, cons
 
 // ------------------------------------------------------------------ one-sided Jacobi eigensolver
 constexpr int EIG_THREADS = 1024;
-constexpr int EIG_GL = 16;                      // lanes per column pair: one half-warp reads 16 consecutive rows
-                                                // of a column, 128 bytes, conflict-free
-constexpr int EIG_GROUPS = EIG_THREADS / EIG_GL;
 constexpr int EIG_RS = EIG_MAX + 1;             // odd column stride: strided column reads hit distinct banks
 constexpr int EIG_CB = 16;                      // columns per block of the re-orthonormalisation
 constexpr int EIG_QC = EIG_THREADS / 32;        // finished columns per projection chunk (one per warp)
@@ -156,6 +154,75 @@ __device__ __forceinline__ void circle_pair(int t, int k, int rr, int& i, int& j
     const int m = rr - 1;
     if (k == 0) { i = t; j = m; }
     else { i = (t + k) % m; j = (t - k + m) % m; }
+}
+
+// One round of the tournament: every pair (i, j) of round t is handled by EIG_GL lanes (a half-warp reads 16
+// consecutive rows of a column, 128 bytes, conflict-free) that reduce the inner product by shuffles and,
+// when the pair is not yet orthogonal to tol, rotate the two columns and carry their squared norms.
+// The schedule repeats every sweep, so a pair was last compared rr - 1 rounds ago; when neither column has
+// been rotated since (tmod[c] = global round of the last rotation of column c) that comparison found the
+// pair orthogonal to tol and would return the same inner product (only the norms are refreshed each
+// sweep), so it is skipped.  g = sweep * (rr - 1) + t.
+constexpr int EIG_GL = 16;
+constexpr int EIG_GROUPS = EIG_THREADS / EIG_GL;
+__device__ __forceinline__ void jacobi_round(float2* __restrict__ W, float* __restrict__ cn2, int* __restrict__ tmod,
+                                             int r, int rr, int t, int g, bool first_sweep, int tid, float tol,
+                                             int* rotated, unsigned long long& my_pairs, unsigned long long& my_rot) {
+    const int grp = tid / EIG_GL, lane = tid % EIG_GL;
+    const unsigned gmask = ((1u << EIG_GL) - 1u) << ((tid % 32) / EIG_GL * EIG_GL);
+    for (int k = grp; k < rr / 2; k += EIG_GROUPS) {
+        int i, j;
+        circle_pair(t, k, rr, i, j);
+        if (i >= r || j >= r) continue;
+        if (!first_sweep && max(tmod[i], tmod[j]) < g - (rr - 1)) continue;   // uniform over the group
+        float2* wi = W + i * EIG_RS;
+        float2* wj = W + j * EIG_RS;
+        float cr0 = 0.f, ci0 = 0.f, cr1 = 0.f, ci1 = 0.f;   // two chains for instruction-level overlap
+        int row = lane;
+        for (; row + EIG_GL < r; row += 2 * EIG_GL) {
+            const float2 x0 = wi[row], y0 = wj[row], x1 = wi[row + EIG_GL], y1 = wj[row + EIG_GL];
+            cr0 = fmaf(x0.x, y0.x, fmaf(x0.y, y0.y, cr0));    // conj(x) * y
+            ci0 = fmaf(x0.x, y0.y, fmaf(-x0.y, y0.x, ci0));
+            cr1 = fmaf(x1.x, y1.x, fmaf(x1.y, y1.y, cr1));
+            ci1 = fmaf(x1.x, y1.y, fmaf(-x1.y, y1.x, ci1));
+        }
+        if (row < r) {
+            const float2 x0 = wi[row], y0 = wj[row];
+            cr0 = fmaf(x0.x, y0.x, fmaf(x0.y, y0.y, cr0));
+            ci0 = fmaf(x0.x, y0.y, fmaf(-x0.y, y0.x, ci0));
+        }
+        float cr = cr0 + cr1, ci = ci0 + ci1;
+#pragma unroll
+        for (int off = EIG_GL / 2; off > 0; off >>= 1) {
+            cr += __shfl_xor_sync(gmask, cr, off);
+            ci += __shfl_xor_sync(gmask, ci, off);
+        }
+        if (lane == 0) ++my_pairs;
+        const float a = cn2[i], b = cn2[j];
+        const float cabs = sqrtf(cr * cr + ci * ci);
+        // Columns of the scaled matrix whose norms are both below the FP32 resolution of G are round-off:
+        // rotating them never converges and they are orthonormalised afterwards.
+        const float ab = sqrtf(a) * sqrtf(b);
+        if (!(cabs > tol * ab) || !(cabs > 1e-30f) || !(ab > EIG_NOISE)) continue;
+        const float zeta = (b - a) / (2.f * cabs);
+        const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+        const float cs = rsqrtf(fmaf(tt, tt, 1.f));
+        const float pr = tt * cs * cr / cabs, pi = tt * cs * ci / cabs;   // p = sin(theta) e
+        // x' = cs x - conj(p) y ;  y' = p x + cs y
+        for (int rw = lane; rw < r; rw += EIG_GL) {
+            const float2 x = wi[rw], y = wj[rw];
+            wi[rw] = make_float2(fmaf(cs, x.x, -fmaf(pr, y.x, pi * y.y)), fmaf(cs, x.y, -fmaf(pr, y.y, -pi * y.x)));
+            wj[rw] = make_float2(fmaf(cs, y.x, fmaf(pr, x.x, -pi * x.y)), fmaf(cs, y.y, fmaf(pr, x.y, pi * x.x)));
+        }
+        if (lane == 0) {
+            cn2[i] = fmaxf(a - tt * cabs, 0.f);
+            cn2[j] = b + tt * cabs;
+            tmod[i] = g;
+            tmod[j] = g;
+            *rotated = 1;
+            ++my_rot;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(EIG_THREADS, 1)
@@ -192,12 +259,12 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
     __syncthreads();
 
     const int rr = r + (r & 1);
-    const int grp = tid / EIG_GL, lane = tid % EIG_GL;
-    const unsigned gmask = ((1u << EIG_GL) - 1u) << ((tid % 32) / EIG_GL * EIG_GL);
     // squared column norms, exact at the start of every sweep and carried through each rotation by
     // |x'|^2 = |x|^2 - t |c|, |y'|^2 = |y|^2 + t |c|, so a pair needs only its inner product
     __shared__ float cn2[EIG_MAX];
     unsigned long long my_pairs = 0ull, my_rot = 0ull;
+    __shared__ int tmod[EIG_MAX];                // global round of the last rotation of each column
+    for (int j = tid; j < r; j += EIG_THREADS) tmod[j] = -1;
     int sweep = 0;
     bool converged = (r < 2);
     for (; sweep < max_sweeps && !converged; ++sweep) {
@@ -213,62 +280,14 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
         }
         __syncthreads();
         for (int t = 0; t < rr - 1; ++t) {
-            for (int k = grp; k < rr / 2; k += EIG_GROUPS) {
-                int i, j;
-                circle_pair(t, k, rr, i, j);
-                if (i >= r || j >= r) continue;
-                float2* wi = W + i * EIG_RS;
-                float2* wj = W + j * EIG_RS;
-                float cr0 = 0.f, ci0 = 0.f, cr1 = 0.f, ci1 = 0.f;   // two chains for instruction-level overlap
-                int row = lane;
-                for (; row + EIG_GL < r; row += 2 * EIG_GL) {
-                    const float2 x0 = wi[row], y0 = wj[row], x1 = wi[row + EIG_GL], y1 = wj[row + EIG_GL];
-                    cr0 = fmaf(x0.x, y0.x, fmaf(x0.y, y0.y, cr0));    // conj(x) * y
-                    ci0 = fmaf(x0.x, y0.y, fmaf(-x0.y, y0.x, ci0));
-                    cr1 = fmaf(x1.x, y1.x, fmaf(x1.y, y1.y, cr1));
-                    ci1 = fmaf(x1.x, y1.y, fmaf(-x1.y, y1.x, ci1));
-                }
-                if (row < r) {
-                    const float2 x0 = wi[row], y0 = wj[row];
-                    cr0 = fmaf(x0.x, y0.x, fmaf(x0.y, y0.y, cr0));
-                    ci0 = fmaf(x0.x, y0.y, fmaf(-x0.y, y0.x, ci0));
-                }
-                float cr = cr0 + cr1, ci = ci0 + ci1;
-#pragma unroll
-                for (int off = EIG_GL / 2; off > 0; off >>= 1) {
-                    cr += __shfl_xor_sync(gmask, cr, off);
-                    ci += __shfl_xor_sync(gmask, ci, off);
-                }
-                ++my_pairs;
-                const float a = cn2[i], b = cn2[j];
-                const float cabs = sqrtf(cr * cr + ci * ci);
-                // Columns of the scaled matrix whose norms are both below the FP32 resolution of G are
-                // round-off: rotating them never converges and they are orthonormalised afterwards.
-                const float ab = sqrtf(a) * sqrtf(b);
-                if (!(cabs > tol * ab) || !(cabs > 1e-30f) || !(ab > EIG_NOISE)) continue;
-                const float zeta = (b - a) / (2.f * cabs);
-                const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
-                const float cs = rsqrtf(fmaf(tt, tt, 1.f));
-                const float pr = tt * cs * cr / cabs, pi = tt * cs * ci / cabs;   // p = sin(theta) e
-                // x' = cs x - conj(p) y ;  y' = p x + cs y
-                for (int rw = lane; rw < r; rw += EIG_GL) {
-                    const float2 x = wi[rw], y = wj[rw];
-                    wi[rw] = make_float2(fmaf(cs, x.x, -fmaf(pr, y.x, pi * y.y)), fmaf(cs, x.y, -fmaf(pr, y.y, -pi * y.x)));
-                    wj[rw] = make_float2(fmaf(cs, y.x, fmaf(pr, x.x, -pi * x.y)), fmaf(cs, y.y, fmaf(pr, x.y, pi * x.x)));
-                }
-                if (lane == 0) {
-                    cn2[i] = fmaxf(a - tt * cabs, 0.f);
-                    cn2[j] = b + tt * cabs;
-                    rotated = 1;
-                    ++my_rot;
-                }
-            }
+            jacobi_round(W, cn2, tmod, r, rr, t, sweep * (rr - 1) + t, sweep == 0, tid, tol, &rotated, my_pairs,
+                         my_rot);
             __syncthreads();
         }
         converged = (rotated == 0);
         __syncthreads();
     }
-    if (prof != nullptr && lane == 0 && (my_pairs | my_rot)) {
+    if (prof != nullptr && (my_pairs | my_rot)) {
         atomicAdd(&n_pairs, my_pairs);
         atomicAdd(&n_rot, my_rot);
     }

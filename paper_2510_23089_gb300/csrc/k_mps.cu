@@ -126,13 +126,15 @@ __global__ void k_trace(const double2* __restrict__ G, int ld, Dim rdim, int* __
 
 // Path of the factorisation of an m-row matrix: the shared-memory eigensolver when m <= EIG_MAX, else the
 // range finder on an EIG_MAX-column sketch.
-__global__ void k_path(Dim mdim, int* __restrict__ R, double* __restrict__ ledger) {
+__global__ void k_path(Dim mdim, int chi_max, int* __restrict__ R, double* __restrict__ ledger) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const int m = mdim.eval(R);
     ledger[L_TRACE] = 0.0;
     R[R_RAND] = (m > EIG_MAX) ? 1 : 0;
-    R[R_P] = min(m, EIG_MAX);
-    R[R_ROWS] = min(m, EIG_MAX);
+    // range-finder subspace: the largest rank the truncation may keep plus RF_OVERSAMPLE directions
+    const int P = rf_subspace(m, chi_max);
+    R[R_P] = P;
+    R[R_ROWS] = (m > EIG_MAX) ? P : m;
     R[R_DEP] = 0;
     R[R_PI] = 0;
 }
@@ -200,17 +202,18 @@ __global__ void k_col_norms(const float2* __restrict__ Q, int ld, Dim mdim, Dim 
 constexpr float CGS_DEP = 1e-5f;
 
 template <int NB, int MAXM>
-__device__ __forceinline__ void cgs_block_body(float2* __restrict__ Q, int ld, Dim mdim, int c0,
+__device__ __forceinline__ void cgs_block_body(float2* __restrict__ Q, int ld, Dim mdim, int c0, int ncols,
                                                const float* __restrict__ pre, int* __restrict__ R, int greg,
                                                int decide) {
-    if (R[greg] != 1) return;
+    if (R[greg] != 1 || c0 >= ncols) return;
+    const int nb = min(NB, ncols - c0);        // columns of this block inside the first ncols
     extern __shared__ float2 S[];              // column-major, S[c * MAXM + row]
     __shared__ float cr_s[NB], ci_s[NB], red[32];
     __shared__ float nrm;
     const int m = mdim.eval(R);
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-    for (int e = tid; e < m * NB; e += blockDim.x) {
-        const int row = e / NB, c = e % NB;
+    for (int e = tid; e < m * nb; e += blockDim.x) {
+        const int row = e / nb, c = e % nb;
         S[c * MAXM + row] = Q[(long long)row * ld + c0 + c];
     }
     __syncthreads();
@@ -229,7 +232,7 @@ __device__ __forceinline__ void cgs_block_body(float2* __restrict__ Q, int ld, D
         return nrm;
     };
     bool dep = false;
-    for (int c = 0; c < NB; ++c) {
+    for (int c = 0; c < nb; ++c) {
         float2* w = S + c * MAXM;
         const float nraw = norm_of(w);
         // first run: dependent on the finished blocks when the projection left less than CGS_DEP of the
@@ -276,23 +279,23 @@ __device__ __forceinline__ void cgs_block_body(float2* __restrict__ Q, int ld, D
         __syncthreads();
     }
     if (tid == 0 && dep) R[R_DEP] = 1;
-    for (int e = tid; e < m * NB; e += blockDim.x) {
-        const int row = e / NB, c = e % NB;
+    for (int e = tid; e < m * nb; e += blockDim.x) {
+        const int row = e / nb, c = e % nb;
         Q[(long long)row * ld + c0 + c] = S[c * MAXM + row];
     }
 }
 
-__global__ void __launch_bounds__(1024) k_cgs_block_32(float2* Q, int ld, Dim mdim, int c0, const float* pre, int* R,
-                                                      int greg, int decide) {
-    cgs_block_body<32, 512>(Q, ld, mdim, c0, pre, R, greg, decide);
+__global__ void __launch_bounds__(1024) k_cgs_block_32(float2* Q, int ld, Dim mdim, int c0, int ncols, const float* pre,
+                                                      int* R, int greg, int decide) {
+    cgs_block_body<32, 512>(Q, ld, mdim, c0, ncols, pre, R, greg, decide);
 }
-__global__ void __launch_bounds__(1024) k_cgs_block_16(float2* Q, int ld, Dim mdim, int c0, const float* pre, int* R,
-                                                      int greg, int decide) {
-    cgs_block_body<16, 1024>(Q, ld, mdim, c0, pre, R, greg, decide);
+__global__ void __launch_bounds__(1024) k_cgs_block_16(float2* Q, int ld, Dim mdim, int c0, int ncols, const float* pre,
+                                                      int* R, int greg, int decide) {
+    cgs_block_body<16, 1024>(Q, ld, mdim, c0, ncols, pre, R, greg, decide);
 }
-__global__ void __launch_bounds__(1024) k_cgs_block_8(float2* Q, int ld, Dim mdim, int c0, const float* pre, int* R,
-                                                      int greg, int decide) {
-    cgs_block_body<8, 2048>(Q, ld, mdim, c0, pre, R, greg, decide);
+__global__ void __launch_bounds__(1024) k_cgs_block_8(float2* Q, int ld, Dim mdim, int c0, int ncols, const float* pre,
+                                                      int* R, int greg, int decide) {
+    cgs_block_body<8, 2048>(Q, ld, mdim, c0, ncols, pre, R, greg, decide);
 }
 
 // Guarded copy of n elements (runs when R[greg] == gval).

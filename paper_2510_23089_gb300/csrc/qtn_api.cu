@@ -21,11 +21,11 @@ __global__ void k_plan_encode(int, int, int*);
 __global__ void k_reset_stats(int*, double*);
 __global__ void k_stage2(const float2*, float2*, const float2*, int, int, int, int, const int*);
 __global__ void k_trace(const double2*, int, Dim, int*, double*);
-__global__ void k_path(Dim, int*, double*);
+__global__ void k_path(Dim, int, int*, double*);
 __global__ void k_total_weight(const float2*, Dim, Dim, Dim, const int*, double*);
-__global__ void k_cgs_block_32(float2*, int, Dim, int, const float*, int*, int, int);
-__global__ void k_cgs_block_16(float2*, int, Dim, int, const float*, int*, int, int);
-__global__ void k_cgs_block_8(float2*, int, Dim, int, const float*, int*, int, int);
+__global__ void k_cgs_block_32(float2*, int, Dim, int, int, const float*, int*, int, int);
+__global__ void k_cgs_block_16(float2*, int, Dim, int, int, const float*, int*, int, int);
+__global__ void k_cgs_block_8(float2*, int, Dim, int, int, const float*, int*, int, int);
 __global__ void k_col_norms(const float2*, int, Dim, Dim, float*, const int*, int);
 __global__ void k_set_pi(int*);
 __global__ void k_copy_guarded(const float2*, float2*, long long, const int*, int, int);
@@ -208,7 +208,8 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
     // with the FP32 refinement pass the first eigen-solve only has to give a rough basis
     const bool refine = (tr.prec == QTN_PLAIN_FP32);
     const float tol1 = refine ? 1e-4f : 1e-6f;
-    k_path<<<1, 1, 0, s>>>(io.m, w.R, w.ledger);
+    const int keep_max = (tr.chi_max > 0) ? std::min(tr.chi_max, chi_cap_out) : chi_cap_out;
+    k_path<<<1, 1, 0, s>>>(io.m, keep_max, w.R, w.ledger);
     CKL();
     // Gram G = A A^dagger of an m x n matrix with row stride ld (FP32 products, FP64 split-K accumulation)
     auto gram = [&](const float2* A, Dim m, Dim ld, Dim n, int m_cap, int guard, bool zero,
@@ -248,7 +249,8 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
     //      U = Q U_B.  No product with G is ever formed, so the FP32 dynamic range is that of T itself.
     if (mc > EIG_MAX) {
         if (mc > CGS_MAXM_ALL) return QTN_ERR_WORKSPACE;
-        const Dim P = dr(R_P);
+        const int Ph = rf_subspace(EIG_MAX + 1, keep_max);   // = R[R_P] on this path
+        const Dim P = dc(Ph);
         k_total_weight<<<grid_for((long long)mc * ncap, 256, c->sm_count), 256, 0, s>>>(io.T, io.n, io.m, io.n,
                                                                                             w.R, w.ledger);
         CKL();
@@ -281,7 +283,7 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
             k_col_norms<<<grid_for((long long)pc * 32, 256, c->sm_count), 256, 0, s>>>(Yb, pc, rows, P, pre, w.R,
                                                                                       greg);
             CKL();
-            for (int b0 = 0; b0 < pc; b0 += CGS_B) {
+            for (int b0 = 0; b0 < Ph; b0 += CGS_B) {
                 for (int pass = 0; pass < (b0 > 0 ? 2 : 1); ++pass) {
                     if (b0 > 0) {
                         GemmDesc g{};                               // Cb = Q[:, :b0]^dagger Y[:, b0:b0+B]
@@ -301,10 +303,11 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
                         CK(launch_gemm(h, rows_cap, CGS_B, b0, w.R, s));
                     }
                     const int decide = (pass == 0);
-                    if (CGS_B == 32) k_cgs_block_32<<<1, 1024, cgs_smem, s>>>(Yb, pc, rows, b0, pre, w.R, greg, decide);
+                    if (CGS_B == 32)
+                        k_cgs_block_32<<<1, 1024, cgs_smem, s>>>(Yb, pc, rows, b0, Ph, pre, w.R, greg, decide);
                     else if (CGS_B == 16)
-                        k_cgs_block_16<<<1, 1024, cgs_smem, s>>>(Yb, pc, rows, b0, pre, w.R, greg, decide);
-                    else k_cgs_block_8<<<1, 1024, cgs_smem, s>>>(Yb, pc, rows, b0, pre, w.R, greg, decide);
+                        k_cgs_block_16<<<1, 1024, cgs_smem, s>>>(Yb, pc, rows, b0, Ph, pre, w.R, greg, decide);
+                    else k_cgs_block_8<<<1, 1024, cgs_smem, s>>>(Yb, pc, rows, b0, Ph, pre, w.R, greg, decide);
                     CKL();
                 }
             }
