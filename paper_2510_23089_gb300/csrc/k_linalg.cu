@@ -146,7 +146,6 @@ constexpr int EIG_RS = EIG_MAX + 1;             // odd column stride: strided co
 constexpr int EIG_CB = 16;                      // columns per block of the re-orthonormalisation
 constexpr int EIG_QC = EIG_THREADS / 32;        // finished columns per projection chunk (one per warp)
 constexpr float EIG_DEP0 = 1e-3f;               // residual below which a column is dependent (first run)
-constexpr float EIG_TOL = 1.0e-6f;
 constexpr float EIG_NOISE = 1.0e-13f;           // |w_i| |w_j| floor (matrix scaled to unit largest diagonal)
 
 __device__ __forceinline__ void circle_pair(int t, int k, int rr, int& i, int& j) {
@@ -228,7 +227,8 @@ __device__ __forceinline__ void jacobi_round(float2* __restrict__ W, float* __re
 __global__ void __launch_bounds__(EIG_THREADS, 1)
 k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restrict__ U, Dim ldud,
              double* __restrict__ lam, const int* __restrict__ Rc, int* __restrict__ Rw, int max_sweeps,
-             double* __restrict__ ledger, int guard_reg, int guard_val, double* __restrict__ prof, float tol) {
+             double* __restrict__ ledger, int guard_reg, int guard_val, double* __restrict__ prof, float tol,
+             float dead_rel) {
     if (guard_reg >= 0 && Rc[guard_reg] != guard_val) return;
     extern __shared__ float2 W[];                // column-major, W[j*EIG_RS + i]
     __shared__ double nrm[EIG_MAX];
@@ -237,7 +237,7 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
     const int r = rdim.eval(Rc);
     const long long ld = ldd.eval(Rc), ldu = ldud.eval(Rc);
     if (r <= 0) return;
-    __shared__ double gscale;
+    __shared__ double gscale, nmax_s;
     __shared__ unsigned long long n_pairs, n_rot;
     const int tid = threadIdx.x;
     if (tid == 0) { n_pairs = 0ull; n_rot = 0ull; }
@@ -312,32 +312,42 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
         }
         rank_of[j] = rk;
         lam[rk] = v;
+        if (rk == 0) nmax_s = v;
     }
     __syncthreads();
     // Re-orthonormalise the columns in descending-eigenvalue order: Jacobi leaves the directions below the
     // FP32 resolution of G non-orthogonal, and the new site must be an isometry.  Blocks of EIG_CB unit
     // columns are projected on the finished columns and orthonormalised internally by Cholesky QR; a second
     // run restores what cancellation took from the first, when some column lost more than 30 % of itself.
-    // A column whose residual falls below EIG_DEP0 in the first run, or loses half of itself in the second,
-    // is numerically dependent: it is set
-    // aside and replaced at the end by a pseudo-random vector orthonormalised the same way, so the basis
-    // stays complete and no weight of the factorised matrix is lost.
+    // A column whose eigenvalue is below dead_rel of the largest carries no direction (its column of G V is
+    // round-off) and is not processed; a column whose residual falls below EIG_DEP0 in the first run, or
+    // loses half of itself in the second, is numerically dependent.  Both are set aside and replaced at the
+    // end by completion vectors orthonormalised the same way, so the basis stays complete and no weight of
+    // the factorised matrix is lost.
     __shared__ int col_of_rank[EIG_MAX];
     __shared__ unsigned char dead[EIG_MAX];          // by rank
     __shared__ float invn[EIG_MAX];
     __shared__ float2 Cs[EIG_QC * EIG_CB];           // projection coefficients (finished chunk x block)
     __shared__ float2 Rb[EIG_CB * EIG_CB];           // Gram of the block, overwritten by its Cholesky factor
     __shared__ unsigned char bdead[EIG_CB];
-    __shared__ int nlive_s;
+    __shared__ int nlive_s, npre_s;
     __shared__ int again_s;                           // the block needs its second run
+    __shared__ float lev[EIG_MAX];                    // leverage of each row over the live columns
     const int warp = tid / 32, wl = tid % 32;
     for (int j = tid; j < r; j += EIG_THREADS) {
         col_of_rank[rank_of[j]] = j;
         const double nj = nrm[j] / gscale;           // column norm in the units of W
         invn[j] = nj > 0.0 ? (float)(1.0 / nj) : 0.f;
-        dead[rank_of[j]] = !(nj > 0.0);
+        dead[rank_of[j]] = !(nj > 0.0) || nrm[j] < (double)dead_rel * nmax_s;
     }
     __syncthreads();
+    // dead ranks form a suffix (ranks descend with the eigenvalue): the first of them ends the main pass
+    if (tid == 0) npre_s = r;
+    __syncthreads();
+    for (int t = tid; t < r; t += EIG_THREADS)
+        if (dead[t] && (t == 0 || !dead[t - 1])) npre_s = t;
+    __syncthreads();
+    const int npre = npre_s;
     for (int e = tid; e < r * r; e += EIG_THREADS) {
         const int j = e / r, row = e % r;
         W[j * EIG_RS + row] = cscale(W[j * EIG_RS + row], invn[j]);
@@ -454,7 +464,7 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
             if (pass == 0 && !again_s) break;
         }
     };
-    for (int t0 = 0; t0 < r; t0 += EIG_CB) {
+    for (int t0 = 0; t0 < npre; t0 += EIG_CB) {
         const int nb = min(EIG_CB, r - t0);
         if (tid < EIG_CB) bdead[tid] = (tid < nb) ? dead[t0 + tid] : 1;
         __syncthreads();
@@ -462,46 +472,78 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
         if (tid < nb) dead[t0 + tid] = bdead[tid];
         __syncthreads();
     }
-    // completion: dependent ranks move to the end (stable), get pseudo-random unit vectors and are
-    // orthonormalised against every column before them
-    if (tid == 0) {                                   // rank_of serves as scratch; it is rewritten below
-        int nl = 0;
-        for (int t = 0; t < r; ++t)
-            if (!dead[t]) rank_of[nl++] = col_of_rank[t];
-        int nd = nl;
-        for (int t = 0; t < r; ++t)
-            if (dead[t]) rank_of[nd++] = col_of_rank[t];
-        for (int t = 0; t < r; ++t) {
-            col_of_rank[t] = rank_of[t];
-            dead[t] = (t >= nl);
+    // Completion: dependent ranks move to the end (stable) and are replaced by unit vectors e_k of the rows
+    // least covered by the live columns (smallest leverage sum_t |w_t(k)|^2), which are nearly orthogonal to
+    // them, so one Cholesky-QR run usually suffices; any completion vector that turns out dependent is
+    // replaced by a pseudo-random vector in a second attempt.
+    int neig = r;                                     // live eigen-columns (ranks below carry eigenvalues)
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if (tid == 0) {                               // rank_of serves as scratch; it is rewritten below
+            int nl = 0;
+            for (int t = 0; t < r; ++t)
+                if (!dead[t]) rank_of[nl++] = col_of_rank[t];
+            int nd = nl;
+            for (int t = 0; t < r; ++t)
+                if (dead[t]) rank_of[nd++] = col_of_rank[t];
+            for (int t = 0; t < r; ++t) {
+                col_of_rank[t] = rank_of[t];
+                dead[t] = (t >= nl);
+            }
+            nlive_s = nl;
         }
-        nlive_s = nl;
-    }
-    __syncthreads();
-    const int nlive = nlive_s;
-    for (int t = nlive + warp; t < r; t += EIG_THREADS / 32) {
-        float2* w = W + col_of_rank[t] * EIG_RS;
-        float ss = 0.f;
-        for (int row = wl; row < r; row += 32) {
-            const float2 v = gauss2(977 + t, row, t);
-            w[row] = v;
-            ss = fmaf(v.x, v.x, fmaf(v.y, v.y, ss));
-        }
-        for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
-        const float inv = ss > 0.f ? rsqrtf(ss) : 0.f;
-        for (int row = wl; row < r; row += 32) w[row] = cscale(w[row], inv);
-    }
-    __syncthreads();
-    for (int t0 = nlive; t0 < r; t0 += EIG_CB) {
-        const int nb = min(EIG_CB, r - t0);
-        if (tid < EIG_CB) bdead[tid] = (tid < nb) ? 0 : 1;
         __syncthreads();
-        ortho_block(t0, nb);
+        const int nlive = nlive_s;
+        if (attempt == 0) neig = nlive;
+        if (nlive == r) break;
+        if (attempt == 0) {
+            for (int row = tid; row < r; row += EIG_THREADS) {
+                float l = 0.f;
+                for (int t = 0; t < nlive; ++t) {
+                    const float2 v = W[col_of_rank[t] * EIG_RS + row];
+                    l = fmaf(v.x, v.x, fmaf(v.y, v.y, l));
+                }
+                lev[row] = l;
+            }
+            for (int e = tid; e < (r - nlive) * r; e += EIG_THREADS)
+                W[col_of_rank[nlive + e / r] * EIG_RS + e % r] = make_float2(0.f, 0.f);
+            __syncthreads();
+            for (int row = tid; row < r; row += EIG_THREADS) {
+                const float l = lev[row];
+                int rk = 0;
+                for (int i = 0; i < r; ++i) {
+                    const float u = lev[i];
+                    rk += (u < l) || (u == l && i < row);
+                }
+                if (rk < r - nlive) W[col_of_rank[nlive + rk] * EIG_RS + row] = make_float2(1.f, 0.f);
+            }
+        } else {
+            for (int t = nlive + warp; t < r; t += EIG_THREADS / 32) {
+                float2* w = W + col_of_rank[t] * EIG_RS;
+                float ss = 0.f;
+                for (int row = wl; row < r; row += 32) {
+                    const float2 v = gauss2(977 + t, row, t);
+                    w[row] = v;
+                    ss = fmaf(v.x, v.x, fmaf(v.y, v.y, ss));
+                }
+                for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
+                const float inv = ss > 0.f ? rsqrtf(ss) : 0.f;
+                for (int row = wl; row < r; row += 32) w[row] = cscale(w[row], inv);
+            }
+        }
+        __syncthreads();
+        for (int t0 = nlive; t0 < r; t0 += EIG_CB) {
+            const int nb = min(EIG_CB, r - t0);
+            if (tid < EIG_CB) bdead[tid] = (tid < nb) ? 0 : 1;
+            __syncthreads();
+            ortho_block(t0, nb);
+            if (tid < nb) dead[t0 + tid] = bdead[tid];
+            __syncthreads();
+        }
     }
     for (int t = tid; t < r; t += EIG_THREADS) {
         const int j = col_of_rank[t];
         rank_of[j] = t;
-        lam[t] = (t < nlive) ? nrm[j] : 0.0;
+        lam[t] = (t < neig) ? nrm[j] : 0.0;
     }
     __syncthreads();
     for (int e = tid; e < r * r; e += EIG_THREADS) {
@@ -520,7 +562,7 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
 
 cudaError_t launch_eig(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, double* lam, const int* R,
                        int r_cap, int max_sweeps, double* ledger, cudaStream_t s, int guard_reg, int guard_val,
-                       float tol, int method) {
+                       float tol, int method, float dead_rel) {
     (void)r_cap;
     size_t smem = (size_t)EIG_MAX * EIG_RS * sizeof(float2);
     static bool configured = false;
@@ -540,7 +582,8 @@ cudaError_t launch_eig(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, doub
     if (method == 0 && use_trd) return launch_eig_trd(G, ld, r, U, ldu, lam, R, s, guard_reg, guard_val);
     count_launch(PROF_EIG, s, true);
     k_eig_jacobi<<<1, EIG_THREADS, smem, s>>>(G, ld, r, U, ldu, lam, R, (int*)R, max_sweeps, ledger, guard_reg,
-                                               guard_val, g_prof_ledger ? g_prof_ledger + L_PROF_EIG : nullptr, tol);
+                                               guard_val, g_prof_ledger ? g_prof_ledger + L_PROF_EIG : nullptr, tol,
+                                               dead_rel);
     count_launch(PROF_EIG, s, false);
     return cudaGetLastError();
 }

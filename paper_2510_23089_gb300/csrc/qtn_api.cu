@@ -208,6 +208,11 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
     // with the FP32 refinement pass the first eigen-solve only has to give a rough basis
     const bool refine = (tr.prec == QTN_PLAIN_FP32);
     const float tol1 = refine ? 1e-4f : 1e-6f;
+    // Eigenvalues below dead_rel of the largest are FP32 round-off of the Gram: the rough first solve hands
+    // those directions to the refinement as completion vectors; the refinement itself only drops what it
+    // cannot rotate (products of eigenvalues below the noise floor of the Jacobi sweeps).
+    const float dead1 = refine ? 1e-6f : 0.f;
+    constexpr float DEAD_REFINE = 1e-13f;
     const int keep_max = (tr.chi_max > 0) ? std::min(tr.chi_max, chi_cap_out) : chi_cap_out;
     k_path<<<1, 1, 0, s>>>(io.m, keep_max, w.R, w.ledger);
     CKL();
@@ -235,7 +240,7 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
     k_trace<<<1, 256, 0, s>>>(w.G64, gld, io.m, w.R, w.ledger);
     CKL();
     CK(launch_eig(w.G64, dc(gld), io.m, w.U, dc(gld), w.lam, w.R, std::min(mc, EIG_MAX), max_sweeps, w.ledger, s,
-                  R_RAND, 0, tol1));
+                  R_RAND, 0, tol1, 0, dead1));
     {
         GemmDesc g{};
         g.A = mat(w.U, dc(gld), dc(1), 1);
@@ -385,7 +390,8 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
             CK(launch_gemm(g, pc, cwid, mc, w.R, s));
             if ((st = gram(w.G32, P, ncol, ncol, pc, 1, false, cwid))) return st;
         }
-        CK(launch_eig(w.G64, dc(gld), P, UB, dc(pc), w.lam, w.R, pc, max_sweeps, w.ledger, s, R_RAND, 1, tol1));
+        CK(launch_eig(w.G64, dc(gld), P, UB, dc(pc), w.lam, w.R, pc, max_sweeps, w.ledger, s, R_RAND, 1, tol1, 0,
+                      dead1));
         {   // U = Q U_B  (m x p, column-major with leading dimension gld)
             GemmDesc g{};
             g.A = mat(Qb, dc(pc), dc(1));
@@ -413,7 +419,8 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
         // keeps every direction accurate relative to its own scale.  U <- U V2 and X is formed again from T.
         // This removes the weight that first-pass eigenvectors leak into numerically null directions.
         if ((st = gram(io.X, rows, io.n, io.n, rcap, -1, true, io.n_cap))) return st;
-        CK(launch_eig(w.G64, dc(gld), rows, w.Y, dc(pc), w.lam, w.R, rcap, max_sweeps, w.ledger, s, -1, 0, 1e-6f, 1));
+        CK(launch_eig(w.G64, dc(gld), rows, w.Y, dc(pc), w.lam, w.R, rcap, max_sweeps, w.ledger, s, -1, 0, 1e-6f, 1,
+                      DEAD_REFINE));
         GemmDesc g{};                                   // U2 = U V2 (column-major, ld gld) in the Q buffer
         g.A = mat(w.U, dc(1), dc(gld));
         g.B = mat(w.Y, dc(1), dc(pc));
