@@ -176,21 +176,28 @@ __device__ __forceinline__ void jacobi_round(float2* __restrict__ W, float* __re
         if (!first_sweep && max(tmod[i], tmod[j]) < g - (rr - 1)) continue;   // uniform over the group
         float2* wi = W + i * EIG_RS;
         float2* wj = W + j * EIG_RS;
-        float cr0 = 0.f, ci0 = 0.f, cr1 = 0.f, ci1 = 0.f;   // two chains for instruction-level overlap
+        float cr0 = 0.f, ci0 = 0.f, cr1 = 0.f, ci1 = 0.f;   // four chains, eight loads in flight
+        float cr2 = 0.f, ci2 = 0.f, cr3 = 0.f, ci3 = 0.f;
         int row = lane;
-        for (; row + EIG_GL < r; row += 2 * EIG_GL) {
+        for (; row + 3 * EIG_GL < r; row += 4 * EIG_GL) {
             const float2 x0 = wi[row], y0 = wj[row], x1 = wi[row + EIG_GL], y1 = wj[row + EIG_GL];
+            const float2 x2 = wi[row + 2 * EIG_GL], y2 = wj[row + 2 * EIG_GL];
+            const float2 x3 = wi[row + 3 * EIG_GL], y3 = wj[row + 3 * EIG_GL];
             cr0 = fmaf(x0.x, y0.x, fmaf(x0.y, y0.y, cr0));    // conj(x) * y
             ci0 = fmaf(x0.x, y0.y, fmaf(-x0.y, y0.x, ci0));
             cr1 = fmaf(x1.x, y1.x, fmaf(x1.y, y1.y, cr1));
             ci1 = fmaf(x1.x, y1.y, fmaf(-x1.y, y1.x, ci1));
+            cr2 = fmaf(x2.x, y2.x, fmaf(x2.y, y2.y, cr2));
+            ci2 = fmaf(x2.x, y2.y, fmaf(-x2.y, y2.x, ci2));
+            cr3 = fmaf(x3.x, y3.x, fmaf(x3.y, y3.y, cr3));
+            ci3 = fmaf(x3.x, y3.y, fmaf(-x3.y, y3.x, ci3));
         }
-        if (row < r) {
+        for (; row < r; row += EIG_GL) {
             const float2 x0 = wi[row], y0 = wj[row];
             cr0 = fmaf(x0.x, y0.x, fmaf(x0.y, y0.y, cr0));
             ci0 = fmaf(x0.x, y0.y, fmaf(-x0.y, y0.x, ci0));
         }
-        float cr = cr0 + cr1, ci = ci0 + ci1;
+        float cr = (cr0 + cr1) + (cr2 + cr3), ci = (ci0 + ci1) + (ci2 + ci3);
 #pragma unroll
         for (int off = EIG_GL / 2; off > 0; off >>= 1) {
             cr += __shfl_xor_sync(gmask, cr, off);
@@ -198,17 +205,32 @@ __device__ __forceinline__ void jacobi_round(float2* __restrict__ W, float* __re
         }
         if (lane == 0) ++my_pairs;
         const float a = cn2[i], b = cn2[j];
-        const float cabs = sqrtf(cr * cr + ci * ci);
+        const float c2 = fmaf(cr, cr, ci * ci);
+        const float ab2 = a * b;
         // Columns of the scaled matrix whose norms are both below the FP32 resolution of G are round-off:
         // rotating them never converges and they are orthonormalised afterwards.
-        const float ab = sqrtf(a) * sqrtf(b);
-        if (!(cabs > tol * ab) || !(cabs > 1e-30f) || !(ab > EIG_NOISE)) continue;
-        const float zeta = (b - a) / (2.f * cabs);
+        if (!(c2 > tol * tol * ab2) || !(c2 > 0.f) || !(ab2 > EIG_NOISE * EIG_NOISE)) continue;
+        const float ic = rsqrtf(c2), cabs = c2 * ic;
+        const float zeta = 0.5f * (b - a) * ic;
         const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
         const float cs = rsqrtf(fmaf(tt, tt, 1.f));
-        const float pr = tt * cs * cr / cabs, pi = tt * cs * ci / cabs;   // p = sin(theta) e
+        const float tc = tt * cs * ic;
+        const float pr = tc * cr, pi = tc * ci;                             // p = sin(theta) e
         // x' = cs x - conj(p) y ;  y' = p x + cs y
-        for (int rw = lane; rw < r; rw += EIG_GL) {
+        int rw = lane;
+        for (; rw + 3 * EIG_GL < r; rw += 4 * EIG_GL) {
+            float2 x[4], y[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { x[u] = wi[rw + u * EIG_GL]; y[u] = wj[rw + u * EIG_GL]; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                wi[rw + u * EIG_GL] = make_float2(fmaf(cs, x[u].x, -fmaf(pr, y[u].x, pi * y[u].y)),
+                                                  fmaf(cs, x[u].y, -fmaf(pr, y[u].y, -pi * y[u].x)));
+                wj[rw + u * EIG_GL] = make_float2(fmaf(cs, y[u].x, fmaf(pr, x[u].x, -pi * x[u].y)),
+                                                  fmaf(cs, y[u].y, fmaf(pr, x[u].y, pi * x[u].x)));
+            }
+        }
+        for (; rw < r; rw += EIG_GL) {
             const float2 x = wi[rw], y = wj[rw];
             wi[rw] = make_float2(fmaf(cs, x.x, -fmaf(pr, y.x, pi * y.y)), fmaf(cs, x.y, -fmaf(pr, y.y, -pi * y.x)));
             wj[rw] = make_float2(fmaf(cs, y.x, fmaf(pr, x.x, -pi * x.y)), fmaf(cs, y.y, fmaf(pr, x.y, pi * x.x)));
@@ -364,11 +386,27 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
                     float2 acc = make_float2(0.f, 0.f);
                     if (c < nb) {
                         const float2* wc = W + col_of_rank[t0 + c] * EIG_RS;
-                        for (int row = h; row < r; row += 2) {
-                            const float2 x = wq[row], y = wc[row];   // conj(x) * y
+                        float2 a1 = make_float2(0.f, 0.f), a2 = a1, a3 = a1;   // four chains
+                        int row = h;
+                        for (; row + 6 < r; row += 8) {
+                            const float2 x0 = wq[row], y0 = wc[row], x1 = wq[row + 2], y1 = wc[row + 2];
+                            const float2 x2 = wq[row + 4], y2 = wc[row + 4], x3 = wq[row + 6], y3 = wc[row + 6];
+                            acc.x = fmaf(x0.x, y0.x, fmaf(x0.y, y0.y, acc.x));   // conj(x) * y
+                            acc.y = fmaf(x0.x, y0.y, fmaf(-x0.y, y0.x, acc.y));
+                            a1.x = fmaf(x1.x, y1.x, fmaf(x1.y, y1.y, a1.x));
+                            a1.y = fmaf(x1.x, y1.y, fmaf(-x1.y, y1.x, a1.y));
+                            a2.x = fmaf(x2.x, y2.x, fmaf(x2.y, y2.y, a2.x));
+                            a2.y = fmaf(x2.x, y2.y, fmaf(-x2.y, y2.x, a2.y));
+                            a3.x = fmaf(x3.x, y3.x, fmaf(x3.y, y3.y, a3.x));
+                            a3.y = fmaf(x3.x, y3.y, fmaf(-x3.y, y3.x, a3.y));
+                        }
+                        for (; row < r; row += 2) {
+                            const float2 x = wq[row], y = wc[row];
                             acc.x = fmaf(x.x, y.x, fmaf(x.y, y.y, acc.x));
                             acc.y = fmaf(x.x, y.y, fmaf(-x.y, y.x, acc.y));
                         }
+                        acc.x += (a1.x + a2.x) + a3.x;
+                        acc.y += (a1.y + a2.y) + a3.y;
                     }
                     acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
                     acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
@@ -378,13 +416,22 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
                 for (int e = tid; e < r * nb; e += EIG_THREADS) {
                     const int c = e / r, row = e % r;
                     float2* wc = W + col_of_rank[t0 + c] * EIG_RS;
-                    float2 acc = wc[row];
-                    for (int q = 0; q < nq; ++q) {
+                    float2 acc = wc[row], acc1 = make_float2(0.f, 0.f);
+                    int q = 0;
+                    for (; q + 1 < nq; q += 2) {
+                        const float2 u0 = W[col_of_rank[qc + q] * EIG_RS + row], k0 = Cs[q * EIG_CB + c];
+                        const float2 u1 = W[col_of_rank[qc + q + 1] * EIG_RS + row], k1 = Cs[(q + 1) * EIG_CB + c];
+                        acc.x -= u0.x * k0.x - u0.y * k0.y;
+                        acc.y -= u0.x * k0.y + u0.y * k0.x;
+                        acc1.x -= u1.x * k1.x - u1.y * k1.y;
+                        acc1.y -= u1.x * k1.y + u1.y * k1.x;
+                    }
+                    if (q < nq) {
                         const float2 u = W[col_of_rank[qc + q] * EIG_RS + row], k = Cs[q * EIG_CB + c];
                         acc.x -= u.x * k.x - u.y * k.y;
                         acc.y -= u.x * k.y + u.y * k.x;
                     }
-                    wc[row] = acc;
+                    wc[row] = make_float2(acc.x + acc1.x, acc.y + acc1.y);
                 }
                 __syncthreads();
             }
@@ -429,15 +476,17 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
                     if (wl > c && wl < nb) Rb[c * EIG_CB + wl] = cscale(Rb[c * EIG_CB + wl], inv);
                     if (wl == c) Rb[c * EIG_CB + c] = make_float2(rcc, 0.f);
                     __syncwarp();
-                    const int mt = nb - c - 1;                // trailing block, upper triangle
-                    for (int p = wl; p < mt * mt; p += 32) {
-                        const int i2 = c + 1 + p / mt, i3 = c + 1 + p % mt;
-                        if (i3 < i2) continue;
-                        const float2 u = Rb[c * EIG_CB + i2], v = Rb[c * EIG_CB + i3];   // conj(u) * v
-                        float2 g = Rb[i2 * EIG_CB + i3];
-                        g.x -= u.x * v.x + u.y * v.y;
-                        g.y -= u.x * v.y - u.y * v.x;
-                        Rb[i2 * EIG_CB + i3] = g;
+                    // trailing block, upper triangle: lane wl owns entries wl + 32 u of the EIG_CB x EIG_CB array
+#pragma unroll
+                    for (int u8 = 0; u8 < EIG_CB * EIG_CB / 32; ++u8) {
+                        const int e = wl + 32 * u8, i2 = e / EIG_CB, i3 = e % EIG_CB;
+                        if (i2 > c && i3 >= i2 && i3 < nb) {
+                            const float2 u = Rb[c * EIG_CB + i2], v = Rb[c * EIG_CB + i3];   // conj(u) * v
+                            float2 g = Rb[e];
+                            g.x -= u.x * v.x + u.y * v.y;
+                            g.y -= u.x * v.y - u.y * v.x;
+                            Rb[e] = g;
+                        }
                     }
                     __syncwarp();
                 }
@@ -449,12 +498,22 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
             for (int row = tid; row < r; row += EIG_THREADS) {
                 for (int c = 0; c < nb; ++c) {
                     float2* wc = W + col_of_rank[t0 + c] * EIG_RS + row;
-                    float2 v = *wc;
-                    for (int k = 0; k < c; ++k) {
+                    float2 v = *wc, v1 = make_float2(0.f, 0.f);
+                    int k = 0;
+                    for (; k + 1 < c; k += 2) {
+                        const float2 x0 = W[col_of_rank[t0 + k] * EIG_RS + row], r0 = Rb[k * EIG_CB + c];
+                        const float2 x1 = W[col_of_rank[t0 + k + 1] * EIG_RS + row], r1 = Rb[(k + 1) * EIG_CB + c];
+                        v.x -= x0.x * r0.x - x0.y * r0.y;
+                        v.y -= x0.x * r0.y + x0.y * r0.x;
+                        v1.x -= x1.x * r1.x - x1.y * r1.y;
+                        v1.y -= x1.x * r1.y + x1.y * r1.x;
+                    }
+                    if (k < c) {
                         const float2 xk = W[col_of_rank[t0 + k] * EIG_RS + row], rk = Rb[k * EIG_CB + c];
                         v.x -= xk.x * rk.x - xk.y * rk.y;
                         v.y -= xk.x * rk.y + xk.y * rk.x;
                     }
+                    v = make_float2(v.x + v1.x, v.y + v1.y);
                     *wc = bdead[c] ? make_float2(0.f, 0.f) : cscale(v, 1.f / Rb[c * EIG_CB + c].x);
                 }
             }
