@@ -38,7 +38,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--prec", choices=["fp32", "mixed"], default="fp32")
+    ap.add_argument("--prec", choices=["fp32", "mixed"], default="fp32",
+                    help="mixed (BF16 tensor-core site contractions) is not built: the library rejects it")
     ap.add_argument("--n", type=int, default=16)
     ap.add_argument("--chi", type=int, default=128)
     ap.add_argument("--cutoff", type=float, default=1e-10)
@@ -50,7 +51,11 @@ def parse():
     ap.add_argument("--workload", choices=["fresnel", "batched"], default="fresnel",
                     help="batched: many independent wavefronts (n 8-12, chi 16-64) stepped as CUDA graphs")
     ap.add_argument("--items", type=int, default=64, help="items of the batched workload")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.prec == "mixed":
+        ap.exit(2, "bench.py: the mixed-precision path (BF16 tensor-core site contractions) is not built; "
+                   "libqtn rejects QTN_MIXED with QTN_ERR_ARG\n")
+    return args
 
 
 def dist_init():

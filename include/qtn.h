@@ -56,8 +56,9 @@ typedef enum {
  *   ONE_D       n sites of d = 2 for a single axis (a vector of 2^n samples). */
 typedef enum { QTN_LAYOUT_SERIAL = 0, QTN_LAYOUT_INTERLEAVED = 1, QTN_LAYOUT_1D = 2 } qtn_layout;
 
-/* Arithmetic of the site contractions.  PLAIN_FP32: FP32 SIMT FMA.
- * MIXED: BF16 tensor-core products with FP32 accumulation (tcgen05). */
+/* Arithmetic of the site contractions.  PLAIN_FP32: FP32 SIMT FMA, FP64-accumulated Grams.
+ * MIXED is reserved for BF16 tensor-core site contractions with FP32 accumulation; it is not built in
+ * this version, and every call that takes a qtn_trunc returns QTN_ERR_ARG for it. */
 typedef enum { QTN_PLAIN_FP32 = 0, QTN_MIXED = 1 } qtn_precision;
 
 /* Canonical form of an MPS, tracked on the host by the library. */

@@ -126,15 +126,13 @@ __global__ void k_trace(const double2* __restrict__ G, int ld, Dim rdim, int* __
 
 // Path of the factorisation of an m-row matrix: the shared-memory eigensolver when m <= EIG_MAX, else the
 // range finder on an EIG_MAX-column sketch.
-__global__ void k_path(Dim mdim, int chi_max, int* __restrict__ R, double* __restrict__ ledger) {
+__global__ void k_path(Dim mdim, int* __restrict__ R, double* __restrict__ ledger) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const int m = mdim.eval(R);
     ledger[L_TRACE] = 0.0;
     R[R_RAND] = (m > EIG_MAX) ? 1 : 0;
-    // range-finder subspace: the largest rank the truncation may keep plus RF_OVERSAMPLE directions
-    const int P = rf_subspace(m, chi_max);
-    R[R_P] = P;
-    R[R_ROWS] = (m > EIG_MAX) ? P : m;
+    R[R_P] = min(m, EIG_MAX);
+    R[R_ROWS] = min(m, EIG_MAX);
     R[R_DEP] = 0;
     R[R_PI] = 0;
 }

@@ -21,7 +21,7 @@ __global__ void k_plan_encode(int, int, int*);
 __global__ void k_reset_stats(int*, double*);
 __global__ void k_stage2(const float2*, float2*, const float2*, int, int, int, int, const int*);
 __global__ void k_trace(const double2*, int, Dim, int*, double*);
-__global__ void k_path(Dim, int, int*, double*);
+__global__ void k_path(Dim, int*, double*);
 __global__ void k_total_weight(const float2*, Dim, Dim, Dim, const int*, double*);
 __global__ void k_cgs_block_32(float2*, int, Dim, int, int, const float*, int*, int, int);
 __global__ void k_cgs_block_16(float2*, int, Dim, int, int, const float*, int*, int, int);
@@ -173,6 +173,12 @@ void add_launches(long long n);
 void prof_begin(bool on, double* ledger);
 void prof_read(int cls, double* ms, long long* launches);
 
+// Truncation rules this build accepts: the FP32 plain path only (QTN_MIXED is reserved), a finite
+// non-negative cutoff.
+static bool trunc_ok(const qtn_trunc& t) {
+    return t.prec == QTN_PLAIN_FP32 && t.cutoff >= 0.0 && isfinite(t.cutoff) && t.max_sweeps >= 0;
+}
+
 // Relative weight below which a direction of an untruncated (gauge-only) sweep is FP32 round-off.
 constexpr double EXACT_CUTOFF = 1e-13;
 
@@ -206,7 +212,7 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
     const int max_sweeps = tr.max_sweeps > 0 ? tr.max_sweeps : 30;
     const int ncap = (int)std::min<long long>(io.n_cap, 1 << 30);
     // with the FP32 refinement pass the first eigen-solve only has to give a rough basis
-    const bool refine = (tr.prec == QTN_PLAIN_FP32);
+    const bool refine = true;
     const float tol1 = refine ? 1e-4f : 1e-6f;
     // Eigenvalues below dead_rel of the largest are FP32 round-off of the Gram: the rough first solve hands
     // those directions to the refinement as completion vectors; the refinement itself only drops what it
@@ -215,8 +221,7 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
     // stays as close to the FP64 result as without the cut (1e-6 doubled both).
     const float dead1 = refine ? 1e-8f : 0.f;
     constexpr float DEAD_REFINE = 1e-13f;
-    const int keep_max = (tr.chi_max > 0) ? std::min(tr.chi_max, chi_cap_out) : chi_cap_out;
-    k_path<<<1, 1, 0, s>>>(io.m, keep_max, w.R, w.ledger);
+    k_path<<<1, 1, 0, s>>>(io.m, w.R, w.ledger);
     CKL();
     // Gram G = A A^dagger of an m x n matrix with row stride ld (FP32 products, FP64 split-K accumulation)
     auto gram = [&](const float2* A, Dim m, Dim ld, Dim n, int m_cap, int guard, bool zero,
@@ -256,7 +261,7 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
     //      U = Q U_B.  No product with G is ever formed, so the FP32 dynamic range is that of T itself.
     if (mc > EIG_MAX) {
         if (mc > CGS_MAXM_ALL) return QTN_ERR_WORKSPACE;
-        const int Ph = rf_subspace(EIG_MAX + 1, keep_max);   // = R[R_P] on this path
+        const int Ph = EIG_MAX;                             // = R[R_P] on this path
         const Dim P = dc(Ph);
         k_total_weight<<<grid_for((long long)mc * ncap, 256, c->sm_count), 256, 0, s>>>(io.T, io.n, io.m, io.n,
                                                                                             w.R, w.ledger);
@@ -642,7 +647,7 @@ qtn_status qtn_workspace_size(void* ctx, int n_sites, int d, int chi_max, int w_
 
 qtn_status qtn_encode(void* ctx, const void* dense, int n, qtn_layout layout, qtn_trunc trunc, qtn_mps* out,
                       qtn_stats* stats, void* ws, size_t ws_bytes) {
-    if (!ctx || !dense || !out || n < 1 || n > 30) return QTN_ERR_ARG;
+    if (!ctx || !dense || !out || n < 1 || n > 30 || !trunc_ok(trunc)) return QTN_ERR_ARG;
     if (layout < QTN_LAYOUT_SERIAL || layout > QTN_LAYOUT_1D) return QTN_ERR_ARG;
     qtn_context* x = (qtn_context*)ctx;
     Ws w;
@@ -731,7 +736,7 @@ static qtn_status apply_inner(qtn_context* x, Ws& w, const qtn_mpo* W, int axis,
 
 qtn_status qtn_apply_mpo(void* ctx, const qtn_mpo* W, int axis, qtn_mps* psi, qtn_trunc trunc, qtn_stats* stats,
                          void* ws, size_t ws_bytes) {
-    if (!ctx || !W || !psi) return QTN_ERR_ARG;
+    if (!ctx || !W || !psi || !trunc_ok(trunc)) return QTN_ERR_ARG;
     qtn_context* x = (qtn_context*)ctx;
     Ws w;
     qtn_status st = bind_ws(x, ws, ws_bytes, w);
@@ -744,7 +749,7 @@ qtn_status qtn_apply_mpo(void* ctx, const qtn_mpo* W, int axis, qtn_mps* psi, qt
 }
 
 qtn_status qtn_truncate(void* ctx, qtn_mps* psi, qtn_trunc trunc, qtn_stats* stats, void* ws, size_t ws_bytes) {
-    if (!ctx || !psi) return QTN_ERR_ARG;
+    if (!ctx || !psi || !trunc_ok(trunc)) return QTN_ERR_ARG;
     qtn_context* x = (qtn_context*)ctx;
     Ws w;
     qtn_status st = bind_ws(x, ws, ws_bytes, w);
@@ -768,7 +773,7 @@ qtn_status qtn_truncate(void* ctx, qtn_mps* psi, qtn_trunc trunc, qtn_stats* sta
 qtn_status qtn_fresnel_step(void* ctx, qtn_mps* psi, qtn_layout layout, const qtn_mpo* qft, const qtn_mpo* qft_dagger,
                             const qtn_mpo* phase, int n_steps, qtn_trunc trunc, qtn_stats* stats, void* ws,
                             size_t ws_bytes) {
-    if (!ctx || !psi || !qft || !qft_dagger || !phase || n_steps < 0) return QTN_ERR_ARG;
+    if (!ctx || !psi || !qft || !qft_dagger || !phase || n_steps < 0 || !trunc_ok(trunc)) return QTN_ERR_ARG;
     qtn_context* x = (qtn_context*)ctx;
     Ws w;
     qtn_status st = bind_ws(x, ws, ws_bytes, w);
@@ -866,7 +871,7 @@ __global__ void k_copy_cols(const float2* __restrict__ U, int ldu, const int* __
 
 qtn_status qtn_tsvd(void* ctx, const void* T, int m, int n, qtn_trunc trunc, void* U, void* C, int k_cap, int* k_out,
                     qtn_stats* stats, void* ws, size_t ws_bytes) {
-    if (!ctx || !T || !U || !C || !k_out || m < 1 || n < 1 || k_cap < 1) return QTN_ERR_ARG;
+    if (!ctx || !T || !U || !C || !k_out || m < 1 || n < 1 || k_cap < 1 || !trunc_ok(trunc)) return QTN_ERR_ARG;
     qtn_context* x = (qtn_context*)ctx;
     Ws w;
     qtn_status st = bind_ws(x, ws, ws_bytes, w);
@@ -962,7 +967,7 @@ qtn_status qtn_hadamard(void* ctx, const qtn_mps* a, const qtn_mps* b, int conj_
 
 qtn_status qtn_hadamard_zipup(void* ctx, const qtn_mps* b, int conj_b, qtn_mps* psi, qtn_trunc trunc,
                               qtn_stats* stats, void* ws, size_t ws_bytes) {
-    if (!ctx || !b || !psi) return QTN_ERR_ARG;
+    if (!ctx || !b || !psi || !trunc_ok(trunc)) return QTN_ERR_ARG;
     if (b->d != 4 || psi->d != 4 || b->n_sites != psi->n_sites) return QTN_ERR_SHAPE;
     if (b->sites == psi->sites) return QTN_ERR_ARG;
     qtn_context* x = (qtn_context*)ctx;
@@ -1183,7 +1188,8 @@ extern "C" {
 qtn_status qtn_batch_create(int count, void* const* ctxs, qtn_mps* items, const qtn_mpo* qft, const qtn_mpo* qft_dagger,
                             const qtn_mpo* phase, int n_steps, qtn_trunc trunc, void* const* ws,
                             const size_t* ws_bytes, void** batch) {
-    if (count < 1 || !ctxs || !items || !qft || !qft_dagger || !phase || !ws || !ws_bytes || !batch || n_steps < 1)
+    if (count < 1 || !ctxs || !items || !qft || !qft_dagger || !phase || !ws || !ws_bytes || !batch || n_steps < 1 ||
+        !trunc_ok(trunc))
         return QTN_ERR_ARG;
     qtn_batch* b = new qtn_batch;
     qtn_status result = QTN_OK;
@@ -1333,7 +1339,7 @@ qtn_status noalloc_device(int dev, NoallocDevice* out) {
 
 extern "C" qtn_status qtn_tsvd_noalloc(const void* T, int m, int n, qtn_trunc trunc, void* U, void* C, int k_cap,
                                        int* k_out, qtn_stats* stats, void* stream) {
-    if (!T || !U || !C || !k_out || m < 1 || n < 1 || k_cap < 1) return QTN_ERR_ARG;
+    if (!T || !U || !C || !k_out || m < 1 || n < 1 || k_cap < 1 || !trunc_ok(trunc)) return QTN_ERR_ARG;
     if (m > QTN_NOALLOC_MAX_M || n > QTN_NOALLOC_MAX_N) {
         fprintf(stderr, "qtn_tsvd_noalloc: a %d x %d matrix exceeds the fixed scratch (m <= %d, n <= %d)\n", m, n,
                 QTN_NOALLOC_MAX_M, QTN_NOALLOC_MAX_N);

@@ -162,17 +162,9 @@ struct Ws {
 
 // Largest eigen/SVD problem solved inside one CTA's shared memory.
 constexpr int EIG_MAX = 160;
-// Directions sketched by the range finder beyond the largest rank a truncation may keep (chi_max), when
-// that sum is below EIG_MAX; with one power iteration this oversampling captures the kept directions to
-// the accuracy of the truncation.
-constexpr int RF_OVERSAMPLE = 32;
-// Subspace size of the range finder for a matrix of m rows whose truncation keeps at most keep_max
-// directions (keep_max <= 0: no limit).  For m > EIG_MAX it depends on keep_max alone.
-__host__ __device__ inline int rf_subspace(int m, int keep_max) {
-    const int target = (keep_max > 0 && keep_max < EIG_MAX - RF_OVERSAMPLE) ? keep_max + RF_OVERSAMPLE : EIG_MAX;
-    const int mm = m < EIG_MAX ? m : EIG_MAX;
-    return mm < target ? mm : target;
-}
+// Subspace size of the range finder (m > EIG_MAX rows) is EIG_MAX whatever chi_max is: a subspace of
+// chi_max + 32 or + 64 left chi-limited truncations of slowly decaying spectra 1e-5 to 1e-3 above the
+// Eckart-Young optimum after one power iteration, EIG_MAX keeps them within 1e-6.
 
 // ------------------------------------------------------------------ launches (defined in the .cu files)
 cudaError_t launch_gemm(const GemmDesc& d, int max_m, int max_n, int max_k, const int* R, cudaStream_t s);

@@ -36,7 +36,8 @@ def test_untruncated_reconstruction(eng, m, n, decay):
 
 
 @pytest.mark.parametrize("m,n,decay,chi", [(64, 96, 0.1, 20), (128, 256, 0.05, 40), (96, 200, 0.02, 64),
-                                           (256, 384, 0.05, 64), (512, 768, 0.02, 128)])
+                                           (256, 384, 0.05, 64), (512, 768, 0.02, 128),
+                                           (300, 260, 0.05, 40)])   # range finder of 72 columns: partial last block
 def test_truncated_matches_eckart_young(eng, m, n, decay, chi):
     T = make(m, n, decay, seed=7 * m + n)
     U, C, st = eng.tsvd(torch.from_numpy(T).cuda(), chi, 0.0)
