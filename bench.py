@@ -401,7 +401,9 @@ def main():
     config = {"workload": f"quantics interleaved 2^{args.n}x2^{args.n} wavefront, chi={args.chi}, "
                           "Gaussian beam x rank-8 smooth phase, lambda z/dx^2=25.3 per step",
               "n_sites": args.n, "d": 4, "chi": args.chi, "cutoff": args.cutoff, "layout": "interleaved",
-              "precision": args.prec, "l2": "flushed between timed steps (state is 8 MB, L2-resident otherwise)"}
+              "precision": args.prec,
+              "l2": f"flushed between timed steps (state capacity {args.n * 4 * args.chi * args.chi * 8 / 2**20:.1f} "
+                    "MiB, L2-resident otherwise)"}
     if args.impl == "reference":
         if rank != 0:
             return
