@@ -7,9 +7,11 @@
 //  * k_eig_jacobi: one-sided (Hestenes) Jacobi on the columns of a Hermitian
 //    positive semidefinite r x r matrix G held in shared memory (r <= 160).
 //    Columns converge to G V = U diag(lambda); normalised columns are the
-//    eigenvectors and their norms the eigenvalues.  Disjoint column pairs of a
-//    round-robin round are processed by 16-lane groups with shuffle reductions;
-//    pairs whose columns have not moved since their last comparison are skipped.
+//    eigenvectors and their norms the eigenvalues.  Block-cyclic ordering: pairs
+//    inside 8-column blocks, then across the blocks of each round-robin block
+//    pair, one warp per block (pair) with shuffle reductions and warp-level
+//    synchronisation; pairs whose columns have not moved since their last
+//    comparison are skipped.
 //  * k_select: the truncation rule on the sorted spectrum (FP64 bookkeeping).
 #include <math.h>
 #include <stdlib.h>
@@ -155,94 +157,107 @@ __device__ __forceinline__ void circle_pair(int t, int k, int rr, int& i, int& j
     else { i = (t + k) % m; j = (t - k + m) % m; }
 }
 
-// One round of the tournament: every pair (i, j) of round t is handled by EIG_GL lanes (a half-warp reads 16
-// consecutive rows of a column, 128 bytes, conflict-free) that reduce the inner product by shuffles and,
-// when the pair is not yet orthogonal to tol, rotate the two columns and carry their squared norms.
-// The schedule repeats every sweep, so a pair was last compared rr - 1 rounds ago; when neither column has
-// been rotated since (tmod[c] = global round of the last rotation of column c) that comparison found the
-// pair orthogonal to tol and would return the same inner product (only the norms are refreshed each
-// sweep), so it is skipped.  g = sweep * (rr - 1) + t.
-constexpr int EIG_GL = 16;
-constexpr int EIG_GROUPS = EIG_THREADS / EIG_GL;
-__device__ __forceinline__ void jacobi_round(float2* __restrict__ W, float* __restrict__ cn2, int* __restrict__ tmod,
-                                             int r, int rr, int t, int g, bool first_sweep, int tid, float tol,
-                                             int* rotated, unsigned long long& my_pairs, unsigned long long& my_rot) {
-    const int grp = tid / EIG_GL, lane = tid % EIG_GL;
-    const unsigned gmask = ((1u << EIG_GL) - 1u) << ((tid % 32) / EIG_GL * EIG_GL);
-    for (int k = grp; k < rr / 2; k += EIG_GROUPS) {
-        int i, j;
-        circle_pair(t, k, rr, i, j);
-        if (i >= r || j >= r) continue;
-        if (!first_sweep && max(tmod[i], tmod[j]) < g - (rr - 1)) continue;   // uniform over the group
-        float2* wi = W + i * EIG_RS;
-        float2* wj = W + j * EIG_RS;
-        float cr0 = 0.f, ci0 = 0.f, cr1 = 0.f, ci1 = 0.f;   // four chains, eight loads in flight
-        float cr2 = 0.f, ci2 = 0.f, cr3 = 0.f, ci3 = 0.f;
-        int row = lane;
-        for (; row + 3 * EIG_GL < r; row += 4 * EIG_GL) {
-            const float2 x0 = wi[row], y0 = wj[row], x1 = wi[row + EIG_GL], y1 = wj[row + EIG_GL];
-            const float2 x2 = wi[row + 2 * EIG_GL], y2 = wj[row + 2 * EIG_GL];
-            const float2 x3 = wi[row + 3 * EIG_GL], y3 = wj[row + 3 * EIG_GL];
-            cr0 = fmaf(x0.x, y0.x, fmaf(x0.y, y0.y, cr0));    // conj(x) * y
-            ci0 = fmaf(x0.x, y0.y, fmaf(-x0.y, y0.x, ci0));
-            cr1 = fmaf(x1.x, y1.x, fmaf(x1.y, y1.y, cr1));
-            ci1 = fmaf(x1.x, y1.y, fmaf(-x1.y, y1.x, ci1));
-            cr2 = fmaf(x2.x, y2.x, fmaf(x2.y, y2.y, cr2));
-            ci2 = fmaf(x2.x, y2.y, fmaf(-x2.y, y2.x, ci2));
-            cr3 = fmaf(x3.x, y3.x, fmaf(x3.y, y3.y, cr3));
-            ci3 = fmaf(x3.x, y3.y, fmaf(-x3.y, y3.x, ci3));
-        }
-        for (; row < r; row += EIG_GL) {
-            const float2 x0 = wi[row], y0 = wj[row];
-            cr0 = fmaf(x0.x, y0.x, fmaf(x0.y, y0.y, cr0));
-            ci0 = fmaf(x0.x, y0.y, fmaf(-x0.y, y0.x, ci0));
-        }
-        float cr = (cr0 + cr1) + (cr2 + cr3), ci = (ci0 + ci1) + (ci2 + ci3);
+// Block-cyclic ordering of a sweep.  Jacobi columns are grouped in blocks of EIG_BS.  A sweep first
+// compares the pairs inside every block (one warp per block: EIG_BS - 1 rounds of EIG_BS / 2 pairs, 8 lanes
+// per pair) and then, for each round of a round-robin over blocks, the EIG_BS^2 pairs across the two
+// blocks of every block pair (one warp per block pair: EIG_BS rounds of the pairs (A_q, B_(q+s) mod EIG_BS),
+// 4 lanes per pair).  Every column pair is compared once per sweep at a fixed slot, the rounds inside a
+// warp synchronise with __syncwarp, and the block barrier runs once per round of blocks: ~20 barriers per
+// sweep at r = 160 instead of r - 1.
+constexpr int EIG_BS = 8;
+
+// Shared-memory slot of Jacobi column c.  Inside every complete group of 16 columns the slots are permuted
+// so that the 8 columns of a block start 8 banks apart (odd column stride: 2 banks per slot), which keeps
+// the 4-lane groups of a warp free of bank conflicts; a trailing partial group keeps its order.  The
+// ordering only decides which slots meet when: the eigenvectors are the normalised slots either way.
+__device__ __forceinline__ int jacobi_slot(int c, int r16) {
+    if (c >= r16) return c;
+    const int b = (c >> 3) & 1, q = c & 7;
+    return (c & ~15) + 2 * b + 4 * (q & 3) + (q >> 2);
+}
+
+// One pair (ci, cj) handled by LPP lanes (lane li of the pair, mask gmask): the inner product from LPP rows
+// in flight four times over, a shuffle reduction, and, when the pair is not orthogonal to tol, the rotation
+// with the squared norms carried.  Slot g of the sweep's SL slots: when neither column has rotated since
+// this pair's comparison one sweep ago (tmod = slot of a column's last rotation), that comparison found the
+// pair orthogonal and would return the same inner product (only the norms are refreshed each sweep), so it
+// is skipped.  Every early return is uniform over the pair's lanes.
+template <int LPP>
+__device__ __forceinline__ void jacobi_pair(float2* __restrict__ W, float* __restrict__ cn2, int* __restrict__ tmod,
+                                            int r, int r16, int col_i, int col_j, int li, unsigned gmask, int g, int SL,
+                                            bool first_sweep, float tol, int* rotated, unsigned long long& my_pairs,
+                                            unsigned long long& my_rot) {
+    if (col_i >= r || col_j >= r) return;
+    const int si = jacobi_slot(col_i, r16), sj = jacobi_slot(col_j, r16);
+    if (!first_sweep && max(tmod[si], tmod[sj]) < g - SL) return;
+    float2* wi = W + si * EIG_RS;
+    float2* wj = W + sj * EIG_RS;
+    float cr0 = 0.f, ci0 = 0.f, cr1 = 0.f, ci1 = 0.f;   // four chains, eight loads in flight
+    float cr2 = 0.f, ci2 = 0.f, cr3 = 0.f, ci3 = 0.f;
+    int row = li;
+    for (; row + 3 * LPP < r; row += 4 * LPP) {
+        const float2 x0 = wi[row], y0 = wj[row], x1 = wi[row + LPP], y1 = wj[row + LPP];
+        const float2 x2 = wi[row + 2 * LPP], y2 = wj[row + 2 * LPP];
+        const float2 x3 = wi[row + 3 * LPP], y3 = wj[row + 3 * LPP];
+        cr0 = fmaf(x0.x, y0.x, fmaf(x0.y, y0.y, cr0));    // conj(x) * y
+        ci0 = fmaf(x0.x, y0.y, fmaf(-x0.y, y0.x, ci0));
+        cr1 = fmaf(x1.x, y1.x, fmaf(x1.y, y1.y, cr1));
+        ci1 = fmaf(x1.x, y1.y, fmaf(-x1.y, y1.x, ci1));
+        cr2 = fmaf(x2.x, y2.x, fmaf(x2.y, y2.y, cr2));
+        ci2 = fmaf(x2.x, y2.y, fmaf(-x2.y, y2.x, ci2));
+        cr3 = fmaf(x3.x, y3.x, fmaf(x3.y, y3.y, cr3));
+        ci3 = fmaf(x3.x, y3.y, fmaf(-x3.y, y3.x, ci3));
+    }
+    for (; row < r; row += LPP) {
+        const float2 x0 = wi[row], y0 = wj[row];
+        cr0 = fmaf(x0.x, y0.x, fmaf(x0.y, y0.y, cr0));
+        ci0 = fmaf(x0.x, y0.y, fmaf(-x0.y, y0.x, ci0));
+    }
+    float cr = (cr0 + cr1) + (cr2 + cr3), ci = (ci0 + ci1) + (ci2 + ci3);
 #pragma unroll
-        for (int off = EIG_GL / 2; off > 0; off >>= 1) {
-            cr += __shfl_xor_sync(gmask, cr, off);
-            ci += __shfl_xor_sync(gmask, ci, off);
-        }
-        if (lane == 0) ++my_pairs;
-        const float a = cn2[i], b = cn2[j];
-        const float c2 = fmaf(cr, cr, ci * ci);
-        const float ab2 = a * b;
-        // Columns of the scaled matrix whose norms are both below the FP32 resolution of G are round-off:
-        // rotating them never converges and they are orthonormalised afterwards.
-        if (!(c2 > tol * tol * ab2) || !(c2 > 0.f) || !(ab2 > EIG_NOISE * EIG_NOISE)) continue;
-        const float ic = rsqrtf(c2), cabs = c2 * ic;
-        const float zeta = 0.5f * (b - a) * ic;
-        const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
-        const float cs = rsqrtf(fmaf(tt, tt, 1.f));
-        const float tc = tt * cs * ic;
-        const float pr = tc * cr, pi = tc * ci;                             // p = sin(theta) e
-        // x' = cs x - conj(p) y ;  y' = p x + cs y
-        int rw = lane;
-        for (; rw + 3 * EIG_GL < r; rw += 4 * EIG_GL) {
-            float2 x[4], y[4];
+    for (int off = LPP / 2; off > 0; off >>= 1) {
+        cr += __shfl_xor_sync(gmask, cr, off);
+        ci += __shfl_xor_sync(gmask, ci, off);
+    }
+    if (li == 0) ++my_pairs;
+    const float a = cn2[si], b = cn2[sj];
+    const float c2 = fmaf(cr, cr, ci * ci);
+    const float ab2 = a * b;
+    // Columns of the scaled matrix whose norms are both below the FP32 resolution of G are round-off:
+    // rotating them never converges and they are orthonormalised afterwards.
+    if (!(c2 > tol * tol * ab2) || !(c2 > 0.f) || !(ab2 > EIG_NOISE * EIG_NOISE)) return;
+    const float ic = rsqrtf(c2), cabs = c2 * ic;
+    const float zeta = 0.5f * (b - a) * ic;
+    const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+    const float cs = rsqrtf(fmaf(tt, tt, 1.f));
+    const float tc = tt * cs * ic;
+    const float pr = tc * cr, pi = tc * ci;                             // p = sin(theta) e
+    // x' = cs x - conj(p) y ;  y' = p x + cs y
+    int rw = li;
+    for (; rw + 3 * LPP < r; rw += 4 * LPP) {
+        float2 x[4], y[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) { x[u] = wi[rw + u * EIG_GL]; y[u] = wj[rw + u * EIG_GL]; }
+        for (int u = 0; u < 4; ++u) { x[u] = wi[rw + u * LPP]; y[u] = wj[rw + u * LPP]; }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                wi[rw + u * EIG_GL] = make_float2(fmaf(cs, x[u].x, -fmaf(pr, y[u].x, pi * y[u].y)),
-                                                  fmaf(cs, x[u].y, -fmaf(pr, y[u].y, -pi * y[u].x)));
-                wj[rw + u * EIG_GL] = make_float2(fmaf(cs, y[u].x, fmaf(pr, x[u].x, -pi * x[u].y)),
-                                                  fmaf(cs, y[u].y, fmaf(pr, x[u].y, pi * x[u].x)));
-            }
+        for (int u = 0; u < 4; ++u) {
+            wi[rw + u * LPP] = make_float2(fmaf(cs, x[u].x, -fmaf(pr, y[u].x, pi * y[u].y)),
+                                           fmaf(cs, x[u].y, -fmaf(pr, y[u].y, -pi * y[u].x)));
+            wj[rw + u * LPP] = make_float2(fmaf(cs, y[u].x, fmaf(pr, x[u].x, -pi * x[u].y)),
+                                           fmaf(cs, y[u].y, fmaf(pr, x[u].y, pi * x[u].x)));
         }
-        for (; rw < r; rw += EIG_GL) {
-            const float2 x = wi[rw], y = wj[rw];
-            wi[rw] = make_float2(fmaf(cs, x.x, -fmaf(pr, y.x, pi * y.y)), fmaf(cs, x.y, -fmaf(pr, y.y, -pi * y.x)));
-            wj[rw] = make_float2(fmaf(cs, y.x, fmaf(pr, x.x, -pi * x.y)), fmaf(cs, y.y, fmaf(pr, x.y, pi * x.x)));
-        }
-        if (lane == 0) {
-            cn2[i] = fmaxf(a - tt * cabs, 0.f);
-            cn2[j] = b + tt * cabs;
-            tmod[i] = g;
-            tmod[j] = g;
-            *rotated = 1;
-            ++my_rot;
-        }
+    }
+    for (; rw < r; rw += LPP) {
+        const float2 x = wi[rw], y = wj[rw];
+        wi[rw] = make_float2(fmaf(cs, x.x, -fmaf(pr, y.x, pi * y.y)), fmaf(cs, x.y, -fmaf(pr, y.y, -pi * y.x)));
+        wj[rw] = make_float2(fmaf(cs, y.x, fmaf(pr, x.x, -pi * x.y)), fmaf(cs, y.y, fmaf(pr, x.y, pi * x.x)));
+    }
+    if (li == 0) {
+        cn2[si] = fmaxf(a - tt * cabs, 0.f);
+        cn2[sj] = b + tt * cabs;
+        tmod[si] = g;
+        tmod[sj] = g;
+        *rotated = 1;
+        ++my_rot;
     }
 }
 
@@ -280,13 +295,16 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
     }
     __syncthreads();
 
-    const int rr = r + (r & 1);
     // squared column norms, exact at the start of every sweep and carried through each rotation by
     // |x'|^2 = |x|^2 - t |c|, |y'|^2 = |y|^2 + t |c|, so a pair needs only its inner product
     __shared__ float cn2[EIG_MAX];
     unsigned long long my_pairs = 0ull, my_rot = 0ull;
-    __shared__ int tmod[EIG_MAX];                // global round of the last rotation of each column
+    __shared__ int tmod[EIG_MAX];                // slot of the last rotation of each column (by shared slot)
     for (int j = tid; j < r; j += EIG_THREADS) tmod[j] = -1;
+    const int nblk = (r + EIG_BS - 1) / EIG_BS, nbr = nblk + (nblk & 1);
+    const int SL = (EIG_BS - 1) + (nbr - 1) * EIG_BS;   // comparison slots per sweep
+    const int r16 = r & ~15;
+    const int warp_j = tid / 32, lane_j = tid % 32;
     int sweep = 0;
     bool converged = (r < 2);
     for (; sweep < max_sweeps && !converged; ++sweep) {
@@ -301,9 +319,32 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
             if (tid % 32 == 0) cn2[j] = s2;
         }
         __syncthreads();
-        for (int t = 0; t < rr - 1; ++t) {
-            jacobi_round(W, cn2, tmod, r, rr, t, sweep * (rr - 1) + t, sweep == 0, tid, tol, &rotated, my_pairs,
-                         my_rot);
+        const int g0 = sweep * SL;
+        if (warp_j < nblk) {                     // pairs inside block warp_j
+            const int k = lane_j >> 3, li = lane_j & 7;
+            const unsigned gmask = 0xFFu << (8 * k);
+            for (int u = 0; u < EIG_BS - 1; ++u) {
+                int a, b;
+                circle_pair(u, k, EIG_BS, a, b);
+                jacobi_pair<8>(W, cn2, tmod, r, r16, warp_j * EIG_BS + a, warp_j * EIG_BS + b, li, gmask, g0 + u, SL,
+                               sweep == 0, tol, &rotated, my_pairs, my_rot);
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        for (int t = 0; t < nbr - 1; ++t) {      // pairs across the blocks of every block pair of round t
+            if (warp_j < nbr / 2) {
+                int A, B;
+                circle_pair(t, warp_j, nbr, A, B);
+                const int q = lane_j >> 2, li = lane_j & 3;
+                const unsigned gmask = 0xFu << (4 * q);
+                for (int s2 = 0; s2 < EIG_BS; ++s2) {
+                    jacobi_pair<4>(W, cn2, tmod, r, r16, A * EIG_BS + q, B * EIG_BS + ((q + s2) & (EIG_BS - 1)), li,
+                                   gmask, g0 + (EIG_BS - 1) + t * EIG_BS + s2, SL, sweep == 0, tol, &rotated, my_pairs,
+                                   my_rot);
+                    __syncwarp();
+                }
+            }
             __syncthreads();
         }
         converged = (rotated == 0);
