@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1)
 k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restrict__ U, Dim ldud,
              double* __restrict__ lam, const int* __restrict__ Rc, int* __restrict__ Rw, int max_sweeps,
              double* __restrict__ ledger, int guard_reg, int guard_val, double* __restrict__ prof, float tol,
-             float dead_rel) {
+             float dead_rel, int report_nonconv) {
     if (guard_reg >= 0 && Rc[guard_reg] != guard_val) return;
     extern __shared__ float2 W[];                // column-major, W[j*EIG_RS + i]
     __shared__ double nrm[EIG_MAX];
@@ -652,7 +652,7 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
     }
     if (tid == 0) {
         atomicMax(&Rw[R_SWEEPS], sweep);
-        if (!converged) atomicOr(&Rw[R_FLAGS], 1);
+        if (!converged && report_nonconv) atomicOr(&Rw[R_FLAGS], 1);
         // algorithmic FLOPs: 8 per row for the inner product of a pair, 24 per row for a rotation,
         // 8 r^3 for the re-orthonormalisation (projections and Cholesky QR, complex)
         if (prof != nullptr)
@@ -662,7 +662,7 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
 
 cudaError_t launch_eig(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, double* lam, const int* R,
                        int r_cap, int max_sweeps, double* ledger, cudaStream_t s, int guard_reg, int guard_val,
-                       float tol, int method, float dead_rel) {
+                       float tol, int method, float dead_rel, bool report_nonconv) {
     (void)r_cap;
     size_t smem = (size_t)EIG_MAX * EIG_RS * sizeof(float2);
     static bool configured = false;
@@ -683,7 +683,7 @@ cudaError_t launch_eig(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, doub
     count_launch(PROF_EIG, s, true);
     k_eig_jacobi<<<1, EIG_THREADS, smem, s>>>(G, ld, r, U, ldu, lam, R, (int*)R, max_sweeps, ledger, guard_reg,
                                                guard_val, g_prof_ledger ? g_prof_ledger + L_PROF_EIG : nullptr, tol,
-                                               dead_rel);
+                                               dead_rel, report_nonconv ? 1 : 0);
     count_launch(PROF_EIG, s, false);
     return cudaGetLastError();
 }

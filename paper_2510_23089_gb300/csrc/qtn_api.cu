@@ -221,6 +221,11 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
     // stays as close to the FP64 result as without the cut (1e-6 doubled both).
     const float dead1 = refine ? 1e-8f : 0.f;
     constexpr float DEAD_REFINE = 1e-13f;
+    // The rough first solve stops after six sweeps (its non-convergence is not reported: the refinement
+    // finishes the job); the refinement's tolerance sits five times above the FP32 rounding of a
+    // 160-term inner product (~6e-7 of |x||y|), below which rotations only chase rounding.
+    const int sweeps1 = refine ? std::min(max_sweeps, 6) : max_sweeps;
+    constexpr float TOL_REFINE = 3e-6f;
     k_path<<<1, 1, 0, s>>>(io.m, w.R, w.ledger);
     CKL();
     // Gram G = A A^dagger of an m x n matrix with row stride ld (FP32 products, FP64 split-K accumulation)
@@ -246,8 +251,8 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
     if ((st = gram(io.T, io.m, io.n, io.n, std::min(mc, EIG_MAX), 0, true, io.n_cap))) return st;
     k_trace<<<1, 256, 0, s>>>(w.G64, gld, io.m, w.R, w.ledger);
     CKL();
-    CK(launch_eig(w.G64, dc(gld), io.m, w.U, dc(gld), w.lam, w.R, std::min(mc, EIG_MAX), max_sweeps, w.ledger, s,
-                  R_RAND, 0, tol1, 0, dead1));
+    CK(launch_eig(w.G64, dc(gld), io.m, w.U, dc(gld), w.lam, w.R, std::min(mc, EIG_MAX), sweeps1, w.ledger, s,
+                  R_RAND, 0, tol1, 0, dead1, !refine));
     {
         GemmDesc g{};
         g.A = mat(w.U, dc(gld), dc(1), 1);
@@ -397,8 +402,8 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
             CK(launch_gemm(g, pc, cwid, mc, w.R, s));
             if ((st = gram(w.G32, P, ncol, ncol, pc, 1, false, cwid))) return st;
         }
-        CK(launch_eig(w.G64, dc(gld), P, UB, dc(pc), w.lam, w.R, pc, max_sweeps, w.ledger, s, R_RAND, 1, tol1, 0,
-                      dead1));
+        CK(launch_eig(w.G64, dc(gld), P, UB, dc(pc), w.lam, w.R, pc, sweeps1, w.ledger, s, R_RAND, 1, tol1, 0,
+                      dead1, !refine));
         {   // U = Q U_B  (m x p, column-major with leading dimension gld)
             GemmDesc g{};
             g.A = mat(Qb, dc(pc), dc(1));
@@ -426,7 +431,7 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
         // keeps every direction accurate relative to its own scale.  U <- U V2 and X is formed again from T.
         // This removes the weight that first-pass eigenvectors leak into numerically null directions.
         if ((st = gram(io.X, rows, io.n, io.n, rcap, -1, true, io.n_cap))) return st;
-        CK(launch_eig(w.G64, dc(gld), rows, w.Y, dc(pc), w.lam, w.R, rcap, max_sweeps, w.ledger, s, -1, 0, 1e-6f, 1,
+        CK(launch_eig(w.G64, dc(gld), rows, w.Y, dc(pc), w.lam, w.R, rcap, max_sweeps, w.ledger, s, -1, 0, TOL_REFINE, 1,
                       DEAD_REFINE));
         GemmDesc g{};                                   // U2 = U V2 (column-major, ld gld) in the Q buffer
         g.A = mat(w.U, dc(1), dc(gld));

@@ -173,6 +173,6 @@ cudaError_t launch_eig_trd(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, 
 cudaError_t launch_refine_basis(const double2* G, Dim ld, Dim r, float2* V, int ldv, const int* R, cudaStream_t s);
 cudaError_t launch_eig(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, double* lam, const int* R,
                        int r_cap, int max_sweeps, double* ledger, cudaStream_t s, int guard_reg = -1, int guard_val = 0,
-                       float tol = 1e-6f, int method = 0, float dead_rel = 0.f);
+                       float tol = 1e-6f, int method = 0, float dead_rel = 0.f, bool report_nonconv = true);
 
 }  // namespace qtn
