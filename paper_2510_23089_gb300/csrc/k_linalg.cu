@@ -662,7 +662,7 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
 
 cudaError_t launch_eig(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, double* lam, const int* R,
                        int r_cap, int max_sweeps, double* ledger, cudaStream_t s, int guard_reg, int guard_val,
-                       float tol, int method, float dead_rel, bool report_nonconv) {
+                       float tol, float dead_rel, bool report_nonconv) {
     (void)r_cap;
     size_t smem = (size_t)EIG_MAX * EIG_RS * sizeof(float2);
     static bool configured = false;
@@ -671,15 +671,6 @@ cudaError_t launch_eig(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, doub
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    // method: 0 = from-scratch solve, 1 = refinement of a nearly diagonal matrix.  Both use one-sided Jacobi
-    // (relative accuracy) unless QTN_EIG=trd selects the Householder-tridiagonal solver for from-scratch
-    // solves (absolute accuracy only; faster on large r).
-    static int use_trd = -1;
-    if (use_trd < 0) {
-        const char* e = getenv("QTN_EIG");
-        use_trd = (e != nullptr && e[0] == 't') ? 1 : 0;
-    }
-    if (method == 0 && use_trd) return launch_eig_trd(G, ld, r, U, ldu, lam, R, s, guard_reg, guard_val);
     count_launch(PROF_EIG, s, true);
     k_eig_jacobi<<<1, EIG_THREADS, smem, s>>>(G, ld, r, U, ldu, lam, R, (int*)R, max_sweeps, ledger, guard_reg,
                                                guard_val, g_prof_ledger ? g_prof_ledger + L_PROF_EIG : nullptr, tol,

@@ -211,20 +211,19 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
     const int pc = w.L.p_cap;
     const int max_sweeps = tr.max_sweeps > 0 ? tr.max_sweeps : 30;
     const int ncap = (int)std::min<long long>(io.n_cap, 1 << 30);
-    // with the FP32 refinement pass the first eigen-solve only has to give a rough basis
-    const bool refine = true;
-    const float tol1 = refine ? 1e-4f : 1e-6f;
+    // The FP32 refinement pass below corrects the first eigen-solve, which only has to give a rough basis.
+    constexpr float tol1 = 1e-4f;
     // Eigenvalues below dead_rel of the largest are FP32 round-off of the Gram: the rough first solve hands
     // those directions to the refinement as completion vectors; the refinement itself only drops what it
     // cannot rotate (products of eigenvalues below the noise floor of the Jacobi sweeps).  At 1e-8 the
     // refinement converges in as many sweeps as from the full first basis and the norm of a Fresnel step
     // stays as close to the FP64 result as without the cut (1e-6 doubled both).
-    const float dead1 = refine ? 1e-8f : 0.f;
+    constexpr float dead1 = 1e-8f;
     constexpr float DEAD_REFINE = 1e-13f;
     // The rough first solve stops after six sweeps (its non-convergence is not reported: the refinement
     // finishes the job); the refinement's tolerance sits five times above the FP32 rounding of a
     // 160-term inner product (~6e-7 of |x||y|), below which rotations only chase rounding.
-    const int sweeps1 = refine ? std::min(max_sweeps, 6) : max_sweeps;
+    const int sweeps1 = std::min(max_sweeps, 6);
     constexpr float TOL_REFINE = 3e-6f;
     k_path<<<1, 1, 0, s>>>(io.m, w.R, w.ledger);
     CKL();
@@ -252,7 +251,7 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
     k_trace<<<1, 256, 0, s>>>(w.G64, gld, io.m, w.R, w.ledger);
     CKL();
     CK(launch_eig(w.G64, dc(gld), io.m, w.U, dc(gld), w.lam, w.R, std::min(mc, EIG_MAX), sweeps1, w.ledger, s,
-                  R_RAND, 0, tol1, 0, dead1, !refine));
+                  R_RAND, 0, tol1, dead1, false));
     {
         GemmDesc g{};
         g.A = mat(w.U, dc(gld), dc(1), 1);
@@ -402,8 +401,8 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
             CK(launch_gemm(g, pc, cwid, mc, w.R, s));
             if ((st = gram(w.G32, P, ncol, ncol, pc, 1, false, cwid))) return st;
         }
-        CK(launch_eig(w.G64, dc(gld), P, UB, dc(pc), w.lam, w.R, pc, sweeps1, w.ledger, s, R_RAND, 1, tol1, 0,
-                      dead1, !refine));
+        CK(launch_eig(w.G64, dc(gld), P, UB, dc(pc), w.lam, w.R, pc, sweeps1, w.ledger, s, R_RAND, 1, tol1, dead1,
+                      false));
         {   // U = Q U_B  (m x p, column-major with leading dimension gld)
             GemmDesc g{};
             g.A = mat(Qb, dc(pc), dc(1));
@@ -425,13 +424,13 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
     }
     const Dim rows = dr(R_ROWS);
     const int rcap = std::min(mc, EIG_MAX);
-    if (refine) {
+    {
         // Refinement: the Gram of the projected rows X = U^dagger T is diagonal up to the FP32 error of the
-        // first eigenbasis; Jacobi on it converges in a couple of sweeps and, unlike the tridiagonal solver,
+        // first eigenbasis; Jacobi on it converges in a couple of sweeps and, unlike a tridiagonal solver,
         // keeps every direction accurate relative to its own scale.  U <- U V2 and X is formed again from T.
         // This removes the weight that first-pass eigenvectors leak into numerically null directions.
         if ((st = gram(io.X, rows, io.n, io.n, rcap, -1, true, io.n_cap))) return st;
-        CK(launch_eig(w.G64, dc(gld), rows, w.Y, dc(pc), w.lam, w.R, rcap, max_sweeps, w.ledger, s, -1, 0, TOL_REFINE, 1,
+        CK(launch_eig(w.G64, dc(gld), rows, w.Y, dc(pc), w.lam, w.R, rcap, max_sweeps, w.ledger, s, -1, 0, TOL_REFINE,
                       DEAD_REFINE));
         GemmDesc g{};                                   // U2 = U V2 (column-major, ld gld) in the Q buffer
         g.A = mat(w.U, dc(1), dc(gld));

@@ -168,11 +168,9 @@ constexpr int EIG_MAX = 160;
 
 // ------------------------------------------------------------------ launches (defined in the .cu files)
 cudaError_t launch_gemm(const GemmDesc& d, int max_m, int max_n, int max_k, const int* R, cudaStream_t s);
-cudaError_t launch_eig_trd(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, double* lam, const int* R,
-                           cudaStream_t s, int guard_reg, int guard_val);
 cudaError_t launch_refine_basis(const double2* G, Dim ld, Dim r, float2* V, int ldv, const int* R, cudaStream_t s);
 cudaError_t launch_eig(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, double* lam, const int* R,
                        int r_cap, int max_sweeps, double* ledger, cudaStream_t s, int guard_reg = -1, int guard_val = 0,
-                       float tol = 1e-6f, int method = 0, float dead_rel = 0.f, bool report_nonconv = true);
+                       float tol = 1e-6f, float dead_rel = 0.f, bool report_nonconv = true);
 
 }  // namespace qtn
