@@ -220,10 +220,10 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
     // stays as close to the FP64 result as without the cut (1e-6 doubled both).
     constexpr float dead1 = 1e-8f;
     constexpr float DEAD_REFINE = 1e-13f;
-    // The rough first solve stops after six sweeps (its non-convergence is not reported: the refinement
+    // The rough first solve stops after four sweeps (its non-convergence is not reported: the refinement
     // finishes the job); the refinement's tolerance sits five times above the FP32 rounding of a
     // 160-term inner product (~6e-7 of |x||y|), below which rotations only chase rounding.
-    const int sweeps1 = std::min(max_sweeps, 6);
+    const int sweeps1 = std::min(max_sweeps, 4);
     constexpr float TOL_REFINE = 3e-6f;
     k_path<<<1, 1, 0, s>>>(io.m, w.R, w.ledger);
     CKL();
