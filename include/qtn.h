@@ -99,7 +99,8 @@ typedef struct {
     int chi_max;
     double cutoff;
     int prec;         /* qtn_precision */
-    int max_sweeps;   /* Jacobi sweep limit per eigen-solve (0 = default 30) */
+    int max_sweeps;   /* Jacobi sweep limit per eigen-solve (0 = default 30); the rough first solve of
+                         each truncation, which the refinement solve corrects, stops after at most 4 */
 } qtn_trunc;
 
 /* Statistics of one call (filled only when a non-NULL pointer is passed). */
