@@ -263,7 +263,7 @@ __device__ __forceinline__ void jacobi_pair(float2* __restrict__ W, float* __res
 
 __global__ void __launch_bounds__(EIG_THREADS, 1)
 k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restrict__ U, Dim ldud,
-             double* __restrict__ lam, const int* __restrict__ Rc, int* __restrict__ Rw, int max_sweeps,
+             double* __restrict__ lam, const int* Rc, int* Rw, int max_sweeps,   // Rc, Rw: one register array
              double* __restrict__ ledger, int guard_reg, int guard_val, double* __restrict__ prof, float tol,
              float dead_rel, int report_nonconv) {
     if (guard_reg >= 0 && Rc[guard_reg] != guard_val) return;
