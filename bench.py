@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3, help="end-to-end steps through host buffers (0 skips them)")
     ap.add_argument("--eager", action="store_true", help="launch every kernel from the host instead of "
                                                            "replaying the step's CUDA graph")
-    ap.add_argument("--workload", choices=["fresnel", "batched"], default="fresnel",
+    ap.add_argument("--workload", choices=["fresnel", "batched", "optics"], default="fresnel",
                     help="batched: many independent wavefronts (n 8-12, chi 16-64) stepped as CUDA graphs")
     ap.add_argument("--items", type=int, default=64, help="items of the batched workload")
     args = ap.parse_args()
@@ -347,6 +347,66 @@ def run_batched(args, local):
     return {"ms": ms, "clocks": clocks, "launches": launches, "hist": hist}
 
 
+def run_optics(args, local):
+    """Mask-gradient workload: per item, the intensity loss of one Fresnel step after a phase mask and its
+    gradient with respect to the mask's site tensors (forward pass, adjoint step, overlap derivative), at
+    n = 12 (4096 x 4096), field chi = 32, mask chi = 16; items one after another on one stream, eager."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2510_23089_gb300 import optics, qtn
+
+    torch.cuda.set_device(local)
+    n, chi, chi_m = 12, 32, 16
+    c = LAMBDA_Z_OVER_DX2 / (1 << n)
+    eng = qtn.Engine(n_sites=n, d=4, chi=64, w=32, dense=1 << (2 * n))
+    prob = optics.IntensityLossProblem(eng, n, c, chi=chi, cutoff=args.cutoff, w_cap=16)
+    items = []
+    for i in range(args.items):
+        E = torch.from_numpy(synth.gaussian_beam_with_rectangles(n, seed=7001 + 3 * i, waist=0.1)).cuda()
+        Em = qtn.MPS(n, 4, chi)
+        eng.encode(E, n, "interleaved", Em, chi, args.cutoff, stats=False)
+        mx, my = synth.smooth_random_phase_mask_factors(n, seed=7002 + 3 * i, strength=0.5)
+        X, Y = qtn.MPS(n, 2, 8), qtn.MPS(n, 2, 8)
+        eng.encode(torch.from_numpy(mx.astype(np.complex64)).cuda(), n, "1d", X, 8, 1e-12, stats=False)
+        eng.encode(torch.from_numpy(my.astype(np.complex64)).cuda(), n, "1d", Y, 8, 1e-12, stats=False)
+        M = qtn.MPS(n, 4, 64)
+        eng.kron_interleave(X, Y, M)
+        eng.truncate(M, chi_m, args.cutoff, stats=False)
+        It = torch.from_numpy(synth.rectangles_target(n, seed=7003 + 3 * i).astype(np.complex64)).cuda()
+        Itm = qtn.MPS(n, 4, chi_m)
+        eng.encode(It, n, "interleaved", Itm, chi_m, args.cutoff, stats=False)
+        del E, It
+        items.append((Em, M, Itm))
+    torch.cuda.synchronize()
+
+    def one_pass():
+        loss = 0.0
+        for Em, M, Itm in items:
+            val, cache = prob.forward(Em, M, Itm)
+            prob.backward(Em, M, cache)
+            loss += val
+        return loss
+
+    for _ in range(args.warmup):
+        one_pass()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(local)
+    launches0 = qtn.load_library().qtn_launch_count()
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        loss = one_pass()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    clocks = sampler.stop()
+    launches = qtn.load_library().qtn_launch_count() - launches0
+    return {"ms": ms, "clocks": clocks, "launches": launches, "loss": loss, "mask_bonds": items[0][1].bonds()}
+
+
 # ----------------------------------------------------------------------------- CPU oracle
 
 def oracle_state(n: int, chi: int, cutoff: float):
@@ -430,6 +490,23 @@ def main():
                                        "n in 8..12, chi in {16,32,64}, one CUDA graph per item on its own stream",
                            "items": r["hist"], "cutoff": args.cutoff, "parallelism": f"replicas x{ws}",
                            "l2": "items stay L2-resident (no flush): the batch is one launch of all graphs"},
+                "clocks": r["clocks"], "gpu_launches": r["launches"], "e2e": None, "roofline": None}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
+    if args.workload == "optics":
+        r = run_optics(args, local)
+        value = args.items * args.steps * ws / (r["ms"] / 1e3)
+        line = {"metric": "intensity-loss forward + mask gradient items/s", "value": value, "unit": "items/s",
+                "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp32",
+                "data": "synthetic",
+                "config": {"workload": f"{args.items} items per step: 4096x4096 interleaved field (n=12, chi=32, "
+                                       "Gaussian beam x random rectangles), smooth phase mask (chi=16), rectangle "
+                                       "target; loss |I - I_t|^2 after one Fresnel step and its gradient with "
+                                       "respect to the mask site tensors", "mask_bonds": r["mask_bonds"],
+                           "cutoff": args.cutoff, "parallelism": f"replicas x{ws}", "launch": "eager",
+                           "l2": "states stay L2-resident (no flush)"},
                 "clocks": r["clocks"], "gpu_launches": r["launches"], "e2e": None, "roofline": None}
         if rank == 0:
             print(json.dumps(line), flush=True)
