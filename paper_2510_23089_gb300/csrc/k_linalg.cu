@@ -16,6 +16,8 @@
 #include <math.h>
 #include <stdlib.h>
 
+#include <atomic>
+
 #include "qtn_internal.cuh"
 
 namespace qtn {
@@ -681,7 +683,7 @@ cudaError_t launch_eig(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, doub
 
 // ------------------------------------------------------------------ launch accounting / profiling
 double* g_prof_ledger = nullptr;
-static long long g_launches = 0;
+static std::atomic<long long> g_launches{0};   // host threads may drive several contexts at once
 static bool g_prof_on = false;
 struct ProfPool {
     cudaEvent_t* ev = nullptr;   // pairs (start, stop)
@@ -691,7 +693,7 @@ struct ProfPool {
 static ProfPool g_pool[PROF_NCLASS];
 
 void count_launch(int cls, cudaStream_t s, bool before) {
-    if (!before) ++g_launches;
+    if (!before) g_launches.fetch_add(1, std::memory_order_relaxed);
     if (!g_prof_on || cls == PROF_OTHER) return;
     ProfPool& p = g_pool[cls];
     if (before) {
@@ -705,8 +707,8 @@ void count_launch(int cls, cudaStream_t s, bool before) {
     }
 }
 
-long long launch_total() { return g_launches; }
-void add_launches(long long n) { g_launches += n; }
+long long launch_total() { return g_launches.load(std::memory_order_relaxed); }
+void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void prof_begin(bool on, double* ledger) {
     g_prof_on = on;
