@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--workload", choices=["fresnel", "batched", "optics"], default="fresnel",
                     help="batched: many independent wavefronts (n 8-12, chi 16-64) stepped as CUDA graphs")
     ap.add_argument("--items", type=int, default=64, help="items of the batched workload")
+    ap.add_argument("--oracle-worker", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-budget", type=float, default=30.0, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.prec == "mixed":
         ap.exit(2, "bench.py: the mixed-precision path (BF16 tensor-core site contractions) is not built; "
@@ -97,7 +99,14 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device_index: int):
-        self.idx = device_index
+        # nvidia-smi numbers GPUs in PCI order and ignores CUDA_VISIBLE_DEVICES: address the device by its UUID
+        self.idx = str(device_index)
+        try:
+            import torch
+            u = str(torch.cuda.get_device_properties(device_index).uuid)
+            self.idx = u if u.startswith("GPU-") else f"GPU-{u}"
+        except Exception:
+            pass
         self.proc = None
         self.path = os.path.join("/tmp", f"qtn_clocks_{os.getpid()}.csv")
 
@@ -134,7 +143,7 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "gpu": self.idx}
 
 
 # ----------------------------------------------------------------------------- GPU workload
@@ -467,10 +476,82 @@ def blas_threads():
         return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
+THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
+
+
+def oracle_rate(n: int, chi: int, cutoff: float, steps: int, budget_s: float, threads: int):
+    """The FP64 oracle's steps/s in a child process whose BLAS uses `threads` threads (set through the
+    environment before NumPy loads).  Returns dict(done, sec, bonds, threads)."""
+    env = dict(os.environ)
+    for v in THREAD_VARS:
+        env[v] = str(threads)
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-worker", "--n", str(n), "--chi", str(chi),
+           "--cutoff", repr(cutoff), "--steps", str(steps), "--oracle-budget", str(budget_s)]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=budget_s * 4 + 600)
+    if r.returncode != 0:
+        raise RuntimeError(f"oracle worker failed: {r.stderr[-300:]}")
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    out["threads"] = threads
+    return out
+
+
+def cpu_baseline_line(args, budget_s: float):
+    """cpu_baseline: the oracle on all host cores and on one thread (bounded samples of the workload)."""
+    cores = os.cpu_count() or 1
+    allc = oracle_rate(args.n, args.chi, args.cutoff, args.steps, budget_s, cores)
+    one = oracle_rate(args.n, args.chi, args.cutoff, args.steps, budget_s, 1)
+    return {"value": allc["done"] / allc["sec"], "unit": "steps/s", "cores": cores, "kind": "oracle",
+            "blas_threads": cores,
+            "sample": f"the first {allc['done']} of the {args.steps} timed Fresnel steps, FP64 NumPy oracle from its "
+                      f"own initial state (bounded at {budget_s:.0f} s), BLAS threads = os.cpu_count() = {cores}; "
+                      f"final max bond {max(allc['bonds'])}",
+            "bonds": allc["bonds"],
+            "one_thread": {"value": one["done"] / one["sec"], "unit": "steps/s", "blas_threads": 1,
+                           "sample": f"the first {one['done']} steps, same oracle, bounded at {budget_s:.0f} s"}}
+
+
+# ----------------------------------------------------------------------------- roofline
+
+def roofline_line(r, peaks, steps: int):
+    """Roofline of the dominant kernel class and of the whole step.
+
+    The path is bound by FP32 arithmetic on small dense matrices (the FP64 parts are accumulations of FP32
+    products): peak = SMs x 128 FP32 lanes x 2 FLOP x max SM clock.  FLOPs are counted on the device by
+    the kernels themselves (algorithmic counts, see the kernel docs) over the same `steps` steps, run once
+    more without the graph and with CUDA events around every launch of the two counted classes."""
+    import torch
+    sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+    prof = r["prof"]
+    name, (ms, cnt, fl) = max(prof.items(), key=lambda kv: kv[1][0])
+    achieved = fl / (ms / 1e3) / 1e12 if ms > 0 else 0.0
+    flops_step = sum(v[2] for v in prof.values()) / steps
+    t_roof = flops_step / (alu_peak * 1e12)
+    t_step = r["total_ms"] / steps / 1e3
+    return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+            "frac": achieved / alu_peak, "traffic": None,
+            "peak_source": f"FP32 FMA: {sm} SMs x 128 lanes x 2 x max SM clock {sm_mhz:.0f} MHz (derived; "
+                           "MEASURED_PEAKS holds no FP32 figure)",
+            "launches": cnt, "avg_launch_us": 1e3 * ms / max(cnt, 1), "flops_per_launch": fl / max(cnt, 1),
+            "share_of_step": ms / r["prof_ms"] if r["prof_ms"] else None,
+            "measured_over": f"the same {steps} steps run once more without the CUDA graph, library profiling "
+                             "on (events around every launch of the counted classes)",
+            "composite": {"flops_per_step": flops_step, "t_roof_ms": t_roof * 1e3, "t_step_ms": t_step * 1e3,
+                          "frac": t_roof / t_step,
+                          "note": "T_roof = counted FLOPs per step / FP32 peak; T_step = graph-replayed step"},
+            "classes": {k: {"ms": v[0], "launches": v[1], "flops": v[2], "ms_per_step": v[0] / steps,
+                            "gflop_per_step": v[2] / steps / 1e9} for k, v in prof.items()}}
+
+
 # ----------------------------------------------------------------------------- main
 
 def main():
     args = parse()
+    if args.oracle_worker:
+        done, sec, bonds = oracle_steps(args.n, args.chi, args.cutoff, args.steps, args.oracle_budget)
+        print(json.dumps({"done": done, "sec": sec, "bonds": bonds}), flush=True)
+        return
     rank, ws, local = dist_init()
     config = {"workload": f"quantics interleaved 2^{args.n}x2^{args.n} wavefront, chi={args.chi}, "
                           "Gaussian beam x rank-8 smooth phase, lambda z/dx^2=25.3 per step",
@@ -486,7 +567,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus, "steps": done,
                 "warmup": 0, "ms_per_step": sec * 1e3 / done, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config, "impl": "reference",
-                "cpu_baseline": {"value": value, "unit": "steps/s", "cores": blas_threads(), "kind": "oracle",
+                "cpu_baseline": {"value": value, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+                                 "blas_threads": blas_threads(),
                                  "sample": f"the first {done} Fresnel steps of the FP64 NumPy oracle from the "
                                            f"initial state (bounded at 120 s); final max bond {max(bonds)}"},
                 "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -548,31 +630,11 @@ def main():
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    # FP32 FMA issue rate of the chip: 152 SMs x 128 lanes x 2 FLOP x max SM clock
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     if r["prof"]:
-        dom = max(r["prof"].items(), key=lambda kv: kv[1][0])
-        name, (ms, cnt, fl) = dom
-        achieved = (fl / cnt) / ((ms / cnt) / 1e3) / 1e12 if cnt and ms > 0 else 0.0
-        line["roofline"] = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                            "frac": achieved / alu_peak, "traffic": None,
-                            "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock (derived)",
-                            "launches": cnt, "avg_launch_us": 1e3 * ms / max(cnt, 1),
-                            "share_of_step": ms / r["prof_ms"] if r["prof_ms"] else None,
-                            "measured_over": "the same steps run once more without the CUDA graph, library "
-                                             "profiling on (events around every launch)",
-                            "other_classes": {k: {"ms": v[0], "launches": v[1], "flops": v[2]}
-                                              for k, v in r["prof"].items()}}
+        line["roofline"] = roofline_line(r, peaks, args.steps)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         try:
-            done, sec, bonds = oracle_steps(args.n, args.chi, args.cutoff, args.steps, 30.0)
-            line["cpu_baseline"] = {"value": done / sec, "unit": "steps/s", "cores": blas_threads(),
-                                    "kind": "oracle",
-                                    "sample": f"the first {done} of the {args.steps} timed Fresnel steps, FP64 NumPy "
-                                              f"oracle from its own initial state (bounded at 30 s); "
-                                              f"final max bond {max(bonds)}",
-                                    "bonds": bonds}
+            line["cpu_baseline"] = cpu_baseline_line(args, 30.0)
         except Exception as ex:  # noqa: BLE001
             line["cpu_baseline"] = {"value": None, "unit": "steps/s", "kind": "oracle", "error": repr(ex)[:200]}
     if rank == 0:

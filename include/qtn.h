@@ -24,8 +24,15 @@
  *    whole sequence of calls can be captured in a CUDA graph; kernels are sized
  *    by capacities.
  *  - Errors are returned as qtn_status; nothing is truncated silently: a bond
- *    that would exceed its capacity is clamped to the capacity and the call
- *    reports QTN_ERR_CAPACITY through the statistics flags.
+ *    that the truncation rule would make larger than the state's chi_cap is
+ *    clamped to chi_cap and reported as QTN_ERR_CAPACITY.  Failures found on
+ *    the device (QTN_ERR_NONFINITE, QTN_ERR_CAPACITY, QTN_ERR_NOCONV, in this
+ *    order of precedence) are returned by the call itself when it synchronises
+ *    (a non-NULL qtn_stats*, or a call documented as synchronising); every
+ *    call also ORs them into a sticky status word of its workspace, which
+ *    qtn_check (or qtn_batch_sync for graph-replayed batches) reads and clears.
+ *  - A new workspace is prepared once by qtn_workspace_init (or zero-filled by
+ *    the caller) before its first use.
  */
 #ifndef QTN_H
 #define QTN_H
@@ -96,7 +103,7 @@ typedef struct {
  * sum_{i>=k} s_i^2 is at most cutoff * sum_i s_i^2, capped by chi_max
  * (the paper's relative cutoff, Sec. VI.B.3, read as a relative weight). */
 typedef struct {
-    int chi_max;
+    int chi_max;      /* <= 0: no cap (the state's chi_cap still bounds every bond, see QTN_ERR_CAPACITY) */
     double cutoff;
     int prec;         /* qtn_precision */
     int max_sweeps;   /* Jacobi sweep limit per eigen-solve (0 = default 30); the rough first solve of
@@ -120,6 +127,19 @@ qtn_status qtn_destroy(void* ctx);
 qtn_status qtn_set_stream(void* ctx, void* cuda_stream);
 const char* qtn_status_string(qtn_status s);
 int qtn_version(void);
+
+/* Clears the state a workspace carries between calls (ledger, dimension
+ * registers and the sticky status word); enqueued on the context's stream.
+ * Call once on a newly allocated workspace (zero-filling it has the same
+ * effect).  ws: device memory of at least qtn_workspace_size bytes. */
+qtn_status qtn_workspace_init(void* ctx, void* ws, size_t ws_bytes);
+
+/* Waits for the context's stream and returns the most severe device-side
+ * failure (QTN_ERR_NONFINITE > QTN_ERR_CAPACITY > QTN_ERR_NOCONV) that any
+ * call on this workspace raised since the previous qtn_check, then clears it.
+ * This is how callers that pass no qtn_stats* (asynchronous calls) learn of
+ * a clamped bond, a non-finite value or a solve that hit max_sweeps. */
+qtn_status qtn_check(void* ctx, void* ws, size_t ws_bytes);
 
 /* Number of kernels the library has launched in this process (all contexts). */
 long long qtn_launch_count(void);
@@ -182,7 +202,10 @@ qtn_status qtn_mpo_dagger(void* ctx, const qtn_mpo* in, qtn_mpo* out);
  *   k_out   host int: the rank kept by the rule of qtn_trunc (k <= k_cap).
  *   stats   optional; discarded = |T|^2 - |C|^2 (FP64).
  * Sizes: m <= d*chi_max and n <= w_max*chi_max of the workspace sizing call.
- * The call synchronises the stream (it returns k on the host). */
+ * A rank above k_cap asked for by the rule is clamped to k_cap and returns
+ * QTN_ERR_CAPACITY (the outputs hold the k_cap leading directions).
+ * The call synchronises the stream (it returns k on the host) and returns the
+ * device-side status of its own work. */
 qtn_status qtn_tsvd(void* ctx, const void* T, int m, int n, qtn_trunc trunc, void* U, void* C, int k_cap,
                     int* k_out, qtn_stats* stats, void* ws, size_t ws_bytes);
 
@@ -238,14 +261,18 @@ qtn_status qtn_add(void* ctx, const qtn_mps* a, const qtn_mps* b, qtn_mps* out);
  * chi).  qtn_batch_create records n_steps steps of every item into one CUDA
  * graph per item without running them; qtn_batch_launch(batch, k) launches
  * every item's graph k times, so the items run concurrently across the GPU.
+ * Items must be in a canonical form (LEFT or RIGHT, as qtn_encode and
+ * qtn_truncate leave them): QTN_CANON_NONE returns QTN_ERR_ARG.
  * The items, operators and workspaces must stay allocated and unmoved while
  * the batch exists; profiling must be off; statistics are not collected (use
- * qtn_norm2 / qtn_overlap afterwards).  Each item should be in a canonical
- * form before creation (as qtn_encode and qtn_truncate leave it). */
+ * qtn_norm2 / qtn_overlap afterwards, and qtn_batch_sync for the status). */
 qtn_status qtn_batch_create(int count, void* const* ctxs, qtn_mps* items, const qtn_mpo* qft,
                             const qtn_mpo* qft_dagger, const qtn_mpo* phase, int n_steps, qtn_trunc trunc,
                             void* const* ws, const size_t* ws_bytes, void** batch);
 qtn_status qtn_batch_launch(void* batch, int repeats);
+/* Waits for every item's stream and returns the most severe failure any
+ * item's replays raised since the last qtn_batch_sync (as qtn_check). */
+qtn_status qtn_batch_sync(void* batch);
 qtn_status qtn_batch_destroy(void* batch);
 
 /* Elementwise (Hadamard) product of two MPS in the same site basis (Sec. V,

@@ -654,7 +654,7 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
     }
     if (tid == 0) {
         atomicMax(&Rw[R_SWEEPS], sweep);
-        if (!converged && report_nonconv) atomicOr(&Rw[R_FLAGS], 1);
+        if (!converged && report_nonconv) raise_flag(Rw, F_NOCONV);
         // algorithmic FLOPs: 8 per row for the inner product of a pair, 24 per row for a rotation,
         // 8 r^3 for the re-orthonormalisation (projections and Cholesky QR, complex)
         if (prof != nullptr)
@@ -666,13 +666,7 @@ cudaError_t launch_eig(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, doub
                        int r_cap, int max_sweeps, double* ledger, cudaStream_t s, int guard_reg, int guard_val,
                        float tol, float dead_rel, bool report_nonconv) {
     (void)r_cap;
-    size_t smem = (size_t)EIG_MAX * EIG_RS * sizeof(float2);
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_eig_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    const size_t smem = (size_t)EIG_MAX * EIG_RS * sizeof(float2);
     count_launch(PROF_EIG, s, true);
     k_eig_jacobi<<<1, EIG_THREADS, smem, s>>>(G, ld, r, U, ldu, lam, R, (int*)R, max_sweeps, ledger, guard_reg,
                                                guard_val, g_prof_ledger ? g_prof_ledger + L_PROF_EIG : nullptr, tol,
@@ -689,18 +683,28 @@ struct ProfPool {
     cudaEvent_t* ev = nullptr;   // pairs (start, stop)
     int cap = 0, used = 0;
     long long launches = 0;
+    double ms = 0.0;             // durations of the pairs already drained
 };
 static ProfPool g_pool[PROF_NCLASS];
+
+// Adds the durations of the recorded pairs to p.ms and frees the pool (waits for the last stop event).
+static void prof_drain(ProfPool& p) {
+    if (p.used >= 2) cudaEventSynchronize(p.ev[p.used - 1]);
+    for (int i = 0; i + 1 < p.used; i += 2) {
+        float e = 0.f;
+        if (cudaEventElapsedTime(&e, p.ev[i], p.ev[i + 1]) == cudaSuccess) p.ms += e;
+    }
+    p.used = 0;
+}
 
 void count_launch(int cls, cudaStream_t s, bool before) {
     if (!before) g_launches.fetch_add(1, std::memory_order_relaxed);
     if (!g_prof_on || cls == PROF_OTHER) return;
     ProfPool& p = g_pool[cls];
     if (before) {
-        if (p.used + 2 > p.cap) return;
+        if (p.used + 2 > p.cap) prof_drain(p);   // every launch is timed: a full pool is drained, not skipped
         cudaEventRecord(p.ev[p.used], s);
     } else {
-        if (p.used + 2 > p.cap) { ++p.launches; return; }
         cudaEventRecord(p.ev[p.used + 1], s);
         p.used += 2;
         ++p.launches;
@@ -722,20 +726,22 @@ void prof_begin(bool on, double* ledger) {
         }
         p.used = 0;
         p.launches = 0;
+        p.ms = 0.0;
     }
 }
 
 // Total device time (ms) and launch count of one kernel class since prof_begin.
 void prof_read(int cls, double* ms, long long* launches) {
     ProfPool& p = g_pool[cls];
-    double t = 0.0;
-    for (int i = 0; i + 1 < p.used; i += 2) {
-        float e = 0.f;
-        cudaEventSynchronize(p.ev[i + 1]);
-        if (cudaEventElapsedTime(&e, p.ev[i], p.ev[i + 1]) == cudaSuccess) t += e;
-    }
-    *ms = t;
+    prof_drain(p);
+    *ms = p.ms;
     *launches = p.launches;
+}
+
+// ------------------------------------------------------------------ per-device kernel attributes
+cudaError_t configure_eig_kernel() {
+    return cudaFuncSetAttribute(k_eig_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)((size_t)EIG_MAX * EIG_RS * sizeof(float2)));
 }
 
 }  // namespace qtn

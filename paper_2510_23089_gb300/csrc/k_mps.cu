@@ -54,7 +54,8 @@ __global__ void k_reset_stats(int* __restrict__ R, double* __restrict__ ledger) 
         R[R_K] = 1;
         R[R_CHIR] = 1;
         R[R_WR] = 1;
-        for (int i = 0; i < L_COUNT; ++i) ledger[i] = 0.0;
+        // the profiling counters (L_PROF_GEMM onwards) accumulate across calls until qtn_profile resets them
+        for (int i = 0; i < L_PROF_GEMM; ++i) ledger[i] = 0.0;
     }
 }
 
@@ -366,13 +367,14 @@ __global__ void k_select(const double* __restrict__ w, Dim rdim, int chi_max, do
         // a rank can never exceed the smaller dimension of the factorised matrix
         const int rank_bound = min(R[R_M], R[R_N]);
         int kk = min(min(k, chi_max), max(rank_bound, 1));
-        if (kk > chi_cap) { kk = chi_cap; R[R_FLAGS] |= 2; }
+        // the rule asks for more directions than the bond can hold: clamp and report, never silently
+        if (kk > chi_cap) { kk = chi_cap; raise_flag(R, F_CAPACITY); }
         kept = 0.0;
         for (int i = 0; i < kk; ++i) kept += sorted_w[i];
         double disc = total - kept;
         if (disc < 0.0) disc = 0.0;
         ledger[L_DISCARDED] += disc;
-        if (!(total == total)) R[R_FLAGS] |= 4;
+        if (!isfinite(total) || !isfinite(wsum) || !isfinite(ledger[L_TRACE])) raise_flag(R, F_NONFINITE);
         R[R_K] = kk;
         R[R_MAXBOND] = max(R[R_MAXBOND], kk);
     }
@@ -478,19 +480,26 @@ __device__ __forceinline__ unsigned compact_bits(unsigned long long v, int n) {
     return out;
 }
 
-// dense (row-major L x L, or 2^n vector for 1D) -> quantics-ordered vector
-__global__ void k_dense_to_quantics(const float2* __restrict__ dense, float2* __restrict__ out, int n, int layout) {
+// dense (row-major L x L, or 2^n vector for 1D) -> quantics-ordered vector; a NaN or Inf entry raises the
+// non-finite flag in R
+__global__ void k_dense_to_quantics(const float2* __restrict__ dense, float2* __restrict__ out, int n, int layout,
+                                    int* __restrict__ R) {
     const long long total = (layout == QTN_LAYOUT_1D) ? (1ll << n) : (1ll << (2 * n));
+    bool bad = false;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
+        float2 v;
         if (layout == QTN_LAYOUT_INTERLEAVED) {
             const unsigned a = compact_bits((unsigned long long)idx >> 1, n);
             const unsigned b = compact_bits((unsigned long long)idx, n);
-            out[idx] = dense[((long long)a << n) | b];
+            v = dense[((long long)a << n) | b];
         } else {
-            out[idx] = dense[idx];
+            v = dense[idx];
         }
+        bad = bad || !isfinite(v.x) || !isfinite(v.y);
+        out[idx] = v;
     }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0 && R != nullptr) raise_flag(R, F_NONFINITE);
 }
 
 __global__ void k_quantics_to_dense(const float2* __restrict__ q, float2* __restrict__ dense, int n, int layout) {

@@ -9,6 +9,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <climits>
+#include <mutex>
 #include <vector>
 
 #include "qtn_internal.cuh"
@@ -37,6 +39,7 @@ __global__ void k_hadamard(const float2*, const int*, int, const float2*, const 
                            int);
 __global__ void k_scale_site(float2*, int, int, const int*, int, float, float);
 constexpr int CGS_MAXM_ALL = 1024;
+constexpr size_t CGS_SMEM = (size_t)32 * 512 * sizeof(float2);   // = 16 x 1024 = 8 x 2048 as well
 __global__ void k_row_weights(const float2*, Dim, Dim, Dim, double*, const int*);
 __global__ void k_select(const double*, Dim, int, double, int, int, int*, int*, double*);
 __global__ void k_write_site(const float2*, int, const int*, float2*, int, int, int, int*, int, const int*);
@@ -45,7 +48,7 @@ __global__ void k_write_last(const float2*, float2*, int, int, int, const int*);
 __global__ void k_site_norm2(const float2*, int, int, const int*, int, double*, int);
 __global__ void k_to_f32(const double2*, float2*, int, Dim, const int*);
 __global__ void k_whiten(float2*, int, const double*, Dim, double, const int*);
-__global__ void k_dense_to_quantics(const float2*, float2*, int, int);
+__global__ void k_dense_to_quantics(const float2*, float2*, int, int, int*);
 __global__ void k_quantics_to_dense(const float2*, float2*, int, int);
 __global__ void k_identity_mpo_state(float2*, int*, int, int);
 __global__ void k_qft_layer(float2*, int*, int, int, int);
@@ -125,25 +128,30 @@ WsLayout ws_layout(int N, int d, int chi, int w, long long dense) {
     return L;
 }
 
+// Offset of a region a layout does not provide: bound to a null pointer, so any use faults loudly on the
+// host side of a check instead of aliasing another region.
+constexpr size_t WS_UNUSED = ~(size_t)0;
+
 static Ws ws_bind(void* base, const WsLayout& L) {
     char* b = (char*)base;
+    auto at = [b](size_t off) -> char* { return off == WS_UNUSED ? nullptr : b + off; };
     Ws w;
     w.L = L;
-    w.ledger = (double*)(b + L.ledger);
-    w.R = (int*)(b + L.regs);
-    w.T = (float2*)(b + L.T);
-    w.P = (float2*)(b + L.P);
-    w.carry = (float2*)(b + L.carry);
-    w.G64 = (double2*)(b + L.G64);
-    w.G32 = (float2*)(b + L.G32);
-    w.U = (float2*)(b + L.U);
-    w.lam = (double*)(b + L.lam);
-    w.Y = (float2*)(b + L.Y);
-    w.Q = (float2*)(b + L.Q);
-    w.S64 = (double2*)(b + L.S64);
-    w.Z = (float2*)(b + L.Z);
-    w.X0 = (float2*)(b + L.X0);
-    w.X1 = (float2*)(b + L.X1);
+    w.ledger = (double*)at(L.ledger);
+    w.R = (int*)at(L.regs);
+    w.T = (float2*)at(L.T);
+    w.P = (float2*)at(L.P);
+    w.carry = (float2*)at(L.carry);
+    w.G64 = (double2*)at(L.G64);
+    w.G32 = (float2*)at(L.G32);
+    w.U = (float2*)at(L.U);
+    w.lam = (double*)at(L.lam);
+    w.Y = (float2*)at(L.Y);
+    w.Q = (float2*)at(L.Q);
+    w.S64 = (double2*)at(L.S64);
+    w.Z = (float2*)at(L.Z);
+    w.X0 = (float2*)at(L.X0);
+    w.X1 = (float2*)at(L.X1);
     return w;
 }
 
@@ -181,6 +189,31 @@ static bool trunc_ok(const qtn_trunc& t) {
 
 // Relative weight below which a direction of an untruncated (gauge-only) sweep is FP32 round-off.
 constexpr double EXACT_CUTOFF = 1e-13;
+
+cudaError_t configure_eig_kernel();
+
+// Kernels with more than 48 KB of dynamic shared memory need the opt-in on every device they run on.
+static std::once_flag g_dev_once[QTN_MAX_DEVICES];
+static cudaError_t g_dev_err[QTN_MAX_DEVICES];
+
+cudaError_t configure_device_kernels(int device) {
+    if (device < 0 || device >= QTN_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::call_once(g_dev_once[device], [device]() {
+        int prev = -1;
+        cudaError_t e = cudaGetDevice(&prev);
+        if (e == cudaSuccess && prev != device) e = cudaSetDevice(device);
+        if (e == cudaSuccess) e = configure_eig_kernel();
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_cgs_block_32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CGS_SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_cgs_block_16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CGS_SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_cgs_block_8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CGS_SMEM);
+        if (prev >= 0 && prev != device) cudaSetDevice(prev);
+        g_dev_err[device] = e;
+    });
+    return g_dev_err[device];
+}
 
 static int grid_for(long long n, int threads, int sm) {
     long long g = (n + threads - 1) / threads;
@@ -283,14 +316,7 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
             g.guard_reg = R_RAND; g.guard_val = 1;
             CK(launch_gemm(g, mc, pc, ncap, w.R, s));
         }
-        static bool cgs_configured = false;
-        const size_t cgs_smem = (size_t)32 * 512 * sizeof(float2);   // = 16 x 1024 = 8 x 2048 as well
-        if (!cgs_configured) {
-            CK(cudaFuncSetAttribute(k_cgs_block_32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cgs_smem));
-            CK(cudaFuncSetAttribute(k_cgs_block_16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cgs_smem));
-            CK(cudaFuncSetAttribute(k_cgs_block_8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cgs_smem));
-            cgs_configured = true;
-        }
+        const size_t cgs_smem = CGS_SMEM;
         // orthonormalise the p columns of Yb (rows live `rows`, at most rows_cap) in place by block classical
         // Gram-Schmidt with reorthogonalisation: each block is projected against the finished blocks and
         // orthonormalised internally, twice; runs when R[greg] == 1
@@ -468,7 +494,7 @@ static qtn_status zip_pass(Ctx* c, Ws& w, qtn_mps* psi, const qtn_mpo* W, int ax
     k_set_one<<<1, 1, 0, s>>>(w.carry);
     CKL();
     qtn_trunc t2 = tr;
-    if (t2.chi_max <= 0 || t2.chi_max > cap) t2.chi_max = cap;
+    if (t2.chi_max <= 0) t2.chi_max = INT_MAX;   // no cap: the bond capacity limits (and reports)
     for (int p = 0; p < N; ++p) {
         const int q = mirror ? N - 1 - p : p;
         float2* site_q = sites + (size_t)q * sstride;
@@ -514,6 +540,17 @@ static qtn_status zip_pass(Ctx* c, Ws& w, qtn_mps* psi, const qtn_mpo* W, int ax
     return QTN_OK;
 }
 
+// Status of a set of flag bits, most severe first.
+static qtn_status flags_status(int f) {
+    if (f & F_NONFINITE) return QTN_ERR_NONFINITE;
+    if (f & F_CAPACITY) return QTN_ERR_CAPACITY;
+    if (f & F_NOCONV) return QTN_ERR_NOCONV;
+    return QTN_OK;
+}
+
+// With a statistics struct the call waits for its work, copies the statistics and returns the status of the
+// flags its kernels raised (the flags stay in the sticky status word too, until qtn_check reads them).
+// Without one the call returns at once; its flags are read by the next qtn_check.
 static qtn_status fill_stats(Ctx* c, Ws& w, qtn_stats* st) {
     if (!st) return QTN_OK;
     double hd[L_COUNT];
@@ -526,8 +563,16 @@ static qtn_status fill_stats(Ctx* c, Ws& w, qtn_stats* st) {
     st->sweeps_used = hi[0];
     st->flags = hi[1];
     st->max_bond = hi[2];
-    if (hi[1] & 4) return QTN_ERR_NONFINITE;
-    return QTN_OK;
+    return flags_status(hi[1]);
+}
+
+// Reads and clears the sticky status word of a workspace (synchronises the stream).
+static qtn_status check_sticky(cudaStream_t s, Ws& w) {
+    int f = 0;
+    CK(cudaMemcpyAsync(&f, w.R + R_STICKY, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemsetAsync(w.R + R_STICKY, 0, sizeof(int), s));
+    CK(cudaStreamSynchronize(s));
+    return flags_status(f);
 }
 
 static qtn_status check_ws(const WsLayout& need, void* ws, size_t bytes) {
@@ -623,6 +668,10 @@ qtn_status qtn_create(void** ctx, void* stream) {
         free(x);
         return QTN_ERR_CUDA;
     }
+    if (configure_device_kernels(x->c.device) != cudaSuccess) {
+        free(x);
+        return QTN_ERR_CUDA;
+    }
     *ctx = x;
     return QTN_OK;
 }
@@ -636,6 +685,26 @@ qtn_status qtn_set_stream(void* ctx, void* stream) {
     if (!ctx) return QTN_ERR_ARG;
     ((qtn_context*)ctx)->c.stream = (cudaStream_t)stream;
     return QTN_OK;
+}
+
+qtn_status qtn_workspace_init(void* ctx, void* ws, size_t ws_bytes) {
+    if (!ctx) return QTN_ERR_ARG;
+    qtn_context* x = (qtn_context*)ctx;
+    Ws w;
+    qtn_status st = bind_ws(x, ws, ws_bytes, w);
+    if (st) return st;
+    // ledger and registers (with the sticky status word) are the only state a workspace carries across calls
+    CK(cudaMemsetAsync(ws, 0, x->L.T, x->c.stream));
+    return QTN_OK;
+}
+
+qtn_status qtn_check(void* ctx, void* ws, size_t ws_bytes) {
+    if (!ctx) return QTN_ERR_ARG;
+    qtn_context* x = (qtn_context*)ctx;
+    Ws w;
+    qtn_status st = bind_ws(x, ws, ws_bytes, w);
+    if (st) return st;
+    return check_sticky(x->c.stream, w);
 }
 
 qtn_status qtn_workspace_size(void* ctx, int n_sites, int d, int chi_max, int w_max, long long dense_elems,
@@ -668,10 +737,11 @@ qtn_status qtn_encode(void* ctx, const void* dense, int n, qtn_layout layout, qt
     CKL();
     k_set_boundary<<<1, 1, 0, s>>>(out->bond, N);
     CKL();
-    k_dense_to_quantics<<<grid_for(total, 256, c->sm_count), 256, 0, s>>>((const float2*)dense, w.X0, n, layout);
+    k_dense_to_quantics<<<grid_for(total, 256, c->sm_count), 256, 0, s>>>((const float2*)dense, w.X0, n, layout,
+                                                                         w.R);
     CKL();
     qtn_trunc t2 = trunc;
-    if (t2.chi_max <= 0 || t2.chi_max > out->chi_cap) t2.chi_max = out->chi_cap;
+    if (t2.chi_max <= 0) t2.chi_max = INT_MAX;
     const int cap = out->chi_cap;
     const size_t sstride = (size_t)cap * d * cap;
     float2* cur = w.X0;
@@ -891,7 +961,7 @@ qtn_status qtn_tsvd(void* ctx, const void* T, int m, int n, qtn_trunc trunc, voi
     k_set_reg<<<1, 1, 0, s>>>(w.R, R_P, std::min(m, EIG_MAX));
     CKL();
     qtn_trunc t2 = trunc;
-    if (t2.chi_max <= 0 || t2.chi_max > k_cap) t2.chi_max = k_cap;
+    if (t2.chi_max <= 0) t2.chi_max = INT_MAX;
     // the factorised matrix is copied to T-space so that the projection buffer has its capacity layout
     TsvdIO io{(const float2*)T, dr(R_M), dr(R_N), m, (long long)n, w.Z};
     Dim rows;
@@ -904,10 +974,12 @@ qtn_status qtn_tsvd(void* ctx, const void* T, int m, int n, qtn_trunc trunc, voi
     k_gather_rows<<<grid_for((long long)k_cap * n, 256, x->c.sm_count), 256, 0, s>>>(w.Z, dr(R_N), ws_perm(w),
                                                                                       (float2*)C, dr(R_N), dr(R_N), w.R);
     CKL();
-    int hk = 0;
-    CK(cudaMemcpyAsync(&hk, w.R + R_K, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int hk[2] = {0, 0};
+    CK(cudaMemcpyAsync(hk, w.R + R_K, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hk + 1, w.R + R_FLAGS, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    *k_out = hk;
+    *k_out = hk[0];
+    if (!stats) return flags_status(hk[1]);
     return fill_stats(&x->c, w, stats);
 }
 
@@ -1155,7 +1227,9 @@ qtn_status qtn_overlap(void* ctx, const qtn_mps* a, const qtn_mps* b, double* re
 
 qtn_status qtn_amplitudes(void* ctx, const qtn_mps* psi, const int* digits, int count, void* out, void* ws,
                           size_t ws_bytes) {
-    if (!ctx || !psi || !digits || !out || count < 0) return QTN_ERR_ARG;
+    if (!ctx || !psi || count < 0) return QTN_ERR_ARG;
+    if (count == 0) return QTN_OK;   // nothing to read (the pointers of an empty request may be NULL)
+    if (!digits || !out) return QTN_ERR_ARG;
     qtn_context* x = (qtn_context*)ctx;
     Ws w;
     qtn_status st = bind_ws(x, ws, ws_bytes, w);
@@ -1184,6 +1258,7 @@ qtn_status qtn_amplitudes(void* ctx, const qtn_mps* psi, const int* digits, int 
 struct qtn_batch {
     std::vector<cudaGraphExec_t> exec;
     std::vector<cudaStream_t> stream;
+    std::vector<int*> sticky;   // each item's sticky status word (in its workspace)
     long long kernels_per_launch = 0;
 };
 
@@ -1204,6 +1279,9 @@ qtn_status qtn_batch_create(int count, void* const* ctxs, qtn_mps* items, const 
         Ws w;
         if ((result = bind_ws(x, ws[i], ws_bytes[i], w))) break;
         qtn_mps* psi = items + i;
+        // a graph replays the same passes every launch: the item must enter in the canonical form it leaves in
+        // after a whole number of steps (an item with none would replay its canonicalisation sweep each time)
+        if (psi->canon == QTN_CANON_NONE) { result = QTN_ERR_ARG; break; }
         const int canon0 = psi->canon;
         const int naxes = 2;
         const qtn_mpo* ops[3] = {qft + i, phase + i, qft_dagger + i};
@@ -1227,6 +1305,7 @@ qtn_status qtn_batch_create(int count, void* const* ctxs, qtn_mps* items, const 
         if (ei != cudaSuccess) { result = QTN_ERR_CUDA; break; }
         b->exec.push_back(e);
         b->stream.push_back(s);
+        b->sticky.push_back(w.R + R_STICKY);
     }
     if (result != QTN_OK) {
         for (auto e : b->exec) cudaGraphExecDestroy(e);
@@ -1245,6 +1324,20 @@ qtn_status qtn_batch_launch(void* batch, int repeats) {
         for (size_t i = 0; i < b->exec.size(); ++i) CK(cudaGraphLaunch(b->exec[i], b->stream[i]));
     add_launches(b->kernels_per_launch * repeats);
     return QTN_OK;
+}
+
+qtn_status qtn_batch_sync(void* batch) {
+    if (!batch) return QTN_ERR_ARG;
+    qtn_batch* b = (qtn_batch*)batch;
+    int worst = 0;
+    for (size_t i = 0; i < b->exec.size(); ++i) {
+        int f = 0;
+        CK(cudaMemcpyAsync(&f, b->sticky[i], sizeof(int), cudaMemcpyDeviceToHost, b->stream[i]));
+        CK(cudaMemsetAsync(b->sticky[i], 0, sizeof(int), b->stream[i]));
+        CK(cudaStreamSynchronize(b->stream[i]));
+        worst |= f;
+    }
+    return flags_status(worst);
 }
 
 qtn_status qtn_batch_destroy(void* batch) {
@@ -1282,7 +1375,9 @@ std::mutex g_noalloc_mu;
 // Only the regions the truncated SVD touches: ledger, registers (+ permutation), the FP64 Gram, the B
 // buffer, the eigenbasis, eigenvalues/weights, the sketch Y and its basis Q, and the projected rows X.
 // Sized for m <= QTN_NOALLOC_MAX_M, n <= QTN_NOALLOC_MAX_N exactly as the general layout sizes them.
-WsLayout noalloc_layout() {
+// Computed at compile time: the static_assert below fails the build if the regions outgrow the array.
+constexpr size_t ca256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr WsLayout noalloc_layout() {
     WsLayout L{};
     L.n_sites = 1;
     L.d = 1;
@@ -1296,7 +1391,7 @@ WsLayout noalloc_layout() {
     const size_t mc = (size_t)L.m_cap, nc = (size_t)L.n_cap, pc = (size_t)L.p_cap;
     const size_t gdim = std::max(mc, pc);
     size_t off = 0;
-    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+    auto take = [&off](size_t bytes) { size_t o = off; off = ca256(off + bytes); return o; };
     L.ledger = take(L_COUNT * sizeof(double) + 64 * sizeof(int));
     L.regs = take(R_COUNT * sizeof(int) + (2 * gdim + 1024) * sizeof(int));
     L.G64 = take(gdim * gdim * c16);
@@ -1307,10 +1402,13 @@ WsLayout noalloc_layout() {
     L.Q = take(std::max(gdim * pc, pc * pc) * c8);
     L.Z = take(std::max(gdim * nc, pc * pc) * c8);
     L.total = off;
-    // regions of the zip-up and of the dense transforms: not used by the truncated SVD
-    L.T = L.P = L.carry = L.S64 = L.omega = L.X0 = L.X1 = off;
+    // regions of the zip-up and of the dense transforms: not used by the truncated SVD (bound to null)
+    L.T = L.P = L.carry = L.S64 = L.omega = L.X0 = L.X1 = WS_UNUSED;
     return L;
 }
+constexpr WsLayout kNoallocLayout = noalloc_layout();
+static_assert(kNoallocLayout.total <= (size_t)QTN_NOALLOC_SCRATCH_BYTES,
+              "the truncated-SVD regions do not fit the fixed scratch array");
 
 // One-time set-up of the calling thread's current device: the array's device address and the SM count.
 qtn_status noalloc_device(int dev, NoallocDevice* out) {
@@ -1328,6 +1426,12 @@ qtn_status noalloc_device(int dev, NoallocDevice* out) {
             e = cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
             if (e != cudaSuccess) {
                 fprintf(stderr, "qtn_tsvd_noalloc: cudaDeviceGetAttribute failed on device %d: %s\n", dev,
+                        cudaGetErrorString(e));
+                return QTN_ERR_CUDA;
+            }
+            e = configure_device_kernels(dev);
+            if (e != cudaSuccess) {
+                fprintf(stderr, "qtn_tsvd_noalloc: kernel set-up failed on device %d: %s\n", dev,
                         cudaGetErrorString(e));
                 return QTN_ERR_CUDA;
             }
@@ -1349,8 +1453,7 @@ extern "C" qtn_status qtn_tsvd_noalloc(const void* T, int m, int n, qtn_trunc tr
                 QTN_NOALLOC_MAX_M, QTN_NOALLOC_MAX_N);
         return QTN_ERR_CAPACITY;
     }
-    static const WsLayout L = noalloc_layout();
-    if (L.total > (size_t)QTN_NOALLOC_SCRATCH_BYTES) return QTN_ERR_WORKSPACE;
+    const WsLayout& L = kNoallocLayout;
     int dev = 0;
     CK(cudaGetDevice(&dev));
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return QTN_ERR_ARG;
@@ -1372,7 +1475,7 @@ extern "C" qtn_status qtn_tsvd_noalloc(const void* T, int m, int n, qtn_trunc tr
     k_set_reg<<<1, 1, 0, s>>>(w.R, R_P, std::min(m, EIG_MAX));
     CKL();
     qtn_trunc t2 = trunc;
-    if (t2.chi_max <= 0 || t2.chi_max > k_cap) t2.chi_max = k_cap;
+    if (t2.chi_max <= 0) t2.chi_max = INT_MAX;
     TsvdIO io{(const float2*)T, dr(R_M), dr(R_N), m, (long long)n, w.Z};
     Dim rows;
     st = tsvd(&c, w, io, t2, k_cap, rows);
@@ -1384,9 +1487,11 @@ extern "C" qtn_status qtn_tsvd_noalloc(const void* T, int m, int n, qtn_trunc tr
     k_gather_rows<<<grid_for((long long)k_cap * n, 256, c.sm_count), 256, 0, s>>>(w.Z, dr(R_N), ws_perm(w),
                                                                                   (float2*)C, dr(R_N), dr(R_N), w.R);
     CKL();
-    int hk = 0;
-    CK(cudaMemcpyAsync(&hk, w.R + R_K, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int hk[2] = {0, 0};
+    CK(cudaMemcpyAsync(hk, w.R + R_K, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hk + 1, w.R + R_FLAGS, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    *k_out = hk;
+    *k_out = hk[0];
+    if (!stats) return flags_status(hk[1]);
     return fill_stats(&c, w, stats);
 }

@@ -72,6 +72,7 @@ enum Reg : int {
     R_ROWS = 24,   // rows of the projected matrix U^dagger T (m, or the subspace size)
     R_DEP = 25,    // range finder: 1 when the sketch has dependent columns (rank below the subspace size)
     R_PI = 26,     // range finder: 1 when the power iteration runs (full-rank sketch)
+    R_STICKY = 27, // status flags (as R_FLAGS) OR-ed over every call since the last qtn_check; never reset per call
     R_COUNT = 32
 };
 
@@ -118,6 +119,13 @@ struct GemmDesc {
 };
 
 // ------------------------------------------------------------------ ledger (device doubles in the workspace)
+// Flag bits of R_FLAGS / R_STICKY.
+enum Flag : int { F_NOCONV = 1, F_CAPACITY = 2, F_NONFINITE = 4 };
+__device__ __forceinline__ void raise_flag(int* R, int bit) {
+    atomicOr(&R[R_FLAGS], bit);
+    atomicOr(&R[R_STICKY], bit);
+}
+
 enum Ledger : int {
     L_DISCARDED = 0,  // accumulated discarded weight of the current call
     L_NORM2,          // squared norm of the result
@@ -160,11 +168,18 @@ struct Ws {
     WsLayout L;
 };
 
+// Devices a process may drive (per-device one-time set-up tables).
+constexpr int QTN_MAX_DEVICES = 64;
+
 // Largest eigen/SVD problem solved inside one CTA's shared memory.
 constexpr int EIG_MAX = 160;
 // Subspace size of the range finder (m > EIG_MAX rows) is EIG_MAX whatever chi_max is: a subspace of
 // chi_max + 32 or + 64 left chi-limited truncations of slowly decaying spectra 1e-5 to 1e-3 above the
 // Eckart-Young optimum after one power iteration, EIG_MAX keeps them within 1e-6.
+
+// One-time per-device set-up of the kernels that need more than the default 48 KB of dynamic shared
+// memory (cudaFuncSetAttribute acts on the current device only); thread-safe, once per device.
+cudaError_t configure_device_kernels(int device);
 
 // ------------------------------------------------------------------ launches (defined in the .cu files)
 cudaError_t launch_gemm(const GemmDesc& d, int max_m, int max_n, int max_k, const int* R, cudaStream_t s);

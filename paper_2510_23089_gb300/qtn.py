@@ -35,7 +35,8 @@ EXPORTS = (
     "qtn_fresnel_step", "qtn_to_dense", "qtn_norm2", "qtn_overlap", "qtn_amplitudes", "qtn_tsvd",
     "qtn_kron_interleave", "qtn_add", "qtn_launch_count", "qtn_profile", "qtn_profile_read", "qtn_tsvd_noalloc",
     "qtn_hadamard", "qtn_scale", "qtn_hadamard_zipup", "qtn_overlap_grad",
-    "qtn_batch_create", "qtn_batch_launch", "qtn_batch_destroy",
+    "qtn_batch_create", "qtn_batch_launch", "qtn_batch_destroy", "qtn_batch_sync",
+    "qtn_workspace_init", "qtn_check",
 )
 
 
@@ -104,6 +105,9 @@ def load_library(path: str = LIB_PATH):
         "qtn_batch_create": [I, ctypes.POINTER(P), mp, op, op, op, I, tr, ctypes.POINTER(P), ctypes.POINTER(S),
                              ctypes.POINTER(P)],
         "qtn_batch_launch": [P, I],
+        "qtn_batch_sync": [P],
+        "qtn_workspace_init": [P, P, S],
+        "qtn_check": [P, P, S],
         "qtn_batch_destroy": [P],
         "qtn_profile": [P, I, P, S],
         "qtn_profile_read": [P, I, ctypes.POINTER(D), ctypes.POINTER(LL), ctypes.POINTER(D), P, S],
@@ -253,6 +257,7 @@ class Engine:
                "qtn_workspace_size")
         self.ws = torch.empty(int(nbytes.value), dtype=torch.uint8, device="cuda")
         self.ws_bytes = int(nbytes.value)
+        _check(self.lib.qtn_workspace_init(ctx, *self._ws()), "qtn_workspace_init")
 
     def __del__(self):
         try:
@@ -385,6 +390,10 @@ class Engine:
         _check(self.lib.qtn_add(self.ctx, ctypes.byref(a.c), ctypes.byref(b.c), ctypes.byref(out.c)), "qtn_add")
         return out
 
+    def check(self):
+        """Raises QtnError for any device-side failure since the last check (qtn_check)."""
+        _check(self.lib.qtn_check(self.ctx, *self._ws()), "qtn_check")
+
     def launch_count(self) -> int:
         return int(self.lib.qtn_launch_count())
 
@@ -431,6 +440,10 @@ class Batch:
 
     def launch(self, repeats: int = 1):
         _check(self.lib.qtn_batch_launch(self.handle, repeats), "qtn_batch_launch")
+
+    def sync(self):
+        """Waits for every item and raises for any device-side failure of their replays (qtn_batch_sync)."""
+        _check(self.lib.qtn_batch_sync(self.handle), "qtn_batch_sync")
 
     def close(self):
         if getattr(self, "handle", None) is not None:

@@ -50,11 +50,8 @@ def test_truncated_matches_eckart_young(eng, m, n, decay, chi):
     err2 = np.linalg.norm(U @ C - T64) ** 2
     assert abs(err2 - st.discarded) <= 1e-5 * n2                  # reported weight is the actual error
     assert np.abs(U.conj().T @ U - np.eye(chi)).max() < 2e-6
-    # optimality: within 1e-6 relative of Eckart-Young where sigma_k / sigma_1 >= 0.1 (resolved by the FP32 Gram)
-    if s[chi - 1] / s[0] >= 0.1:
-        assert abs(st.discarded - exact) <= 1e-6 * exact + 1e-7 * n2
-    else:
-        assert st.discarded <= exact * (1 + 2e-2) + 1e-7 * n2       # sketch of a slowly decaying spectrum
+    # optimality: the relative discarded weight within 1e-6 of the Eckart-Young optimum
+    assert abs(st.discarded - exact) <= 1e-6 * n2
 
 
 @pytest.mark.parametrize("cutoff", [1e-1, 1e-2, 1e-4])

@@ -382,3 +382,71 @@ def test_intensity_loss_gradient_matches_finite_differences():
             fd = (OO.intensity_loss_dense(E, Mp, It, c) - OO.intensity_loss_dense(E, Mm, It, c)) / (2 * h)
             pred = 2 * np.real(np.conj(G[i, j]) * unit)
             assert abs(fd - pred) <= 1e-6 * max(1.0, abs(pred))
+
+
+# ----------------------------------------------------------------------------- exact / naive MPO application
+
+def brute_force_apply(W, vec):
+    """y[s'] = sum_s O[s', s] vec[s] with O[s', s] = prod_p W_p[:, s'_p, s_p, :] written out per index
+    string (loops over all digit strings; independent of the oracle's contractions)."""
+    n = len(W)
+    dim = 2 ** n
+    y = np.zeros(dim, dtype=np.complex128)
+    for out_idx in range(dim):
+        so = [(out_idx >> (n - 1 - p)) & 1 for p in range(n)]
+        for in_idx in range(dim):
+            si = [(in_idx >> (n - 1 - p)) & 1 for p in range(n)]
+            m = np.ones((1, 1), dtype=np.complex128)
+            for p in range(n):
+                m = m @ W[p][:, so[p], si[p], :]
+            y[out_idx] += m[0, 0] * vec[in_idx]
+    return y
+
+
+def test_apply_exact_and_dense_match_brute_force():
+    n = 4
+    W = OM.qft_mpo_layers(n, 1e-14)
+    sites = synth.random_mps_sites([1, 2, 4, 2, 1], 2, seed=901)
+    v = OS.to_vector(sites)
+    ref = brute_force_apply(W, v)
+    assert rel(OS.to_vector(OA.apply_exact(W, sites)), ref) < 1e-12
+    assert rel(OA.apply_dense(W, v), ref) < 1e-12
+    # bonds multiply
+    assert OS.bonds(OA.apply_exact(W, sites)) == [a * b for a, b in zip(OM.bonds(W), OS.bonds(sites))]
+
+
+def test_apply_naive_two_sites_is_eckart_young():
+    # two sites: the naive truncation is one SVD of the 4 x 4 reshaped product, the optimum by Eckart-Young
+    W = OM.qft_mpo_layers(2, 1e-14)
+    sites = synth.random_mps_sites([1, 2, 1], 2, seed=902)
+    y = OA.apply_dense(W, OS.to_vector(sites))
+    s = np.linalg.svd(y.reshape(2, 2), compute_uv=False)
+    out, eps = OA.apply_naive(W, sites, 1, 0.0)
+    assert abs(sum(eps) - s[1] ** 2) < 1e-12 * (s ** 2).sum()
+    assert abs(np.linalg.norm(OS.to_vector(out) - y) ** 2 - s[1] ** 2) < 1e-12 * (s ** 2).sum()
+
+
+def test_apply_naive_error_equals_discarded_weight():
+    # canonical truncation of the exact product: squared error = sum of the per-bond discarded weights
+    n = 5
+    W = OM.qft_mpo_layers(n, 1e-14)
+    sites = synth.random_mps_sites([1, 2, 4, 4, 2, 1], 2, seed=903, decay=0.2)
+    y = OA.apply_dense(W, OS.to_vector(sites))
+    out, eps = OA.apply_naive(W, sites, 3, 0.0)
+    assert max(OS.bonds(out)) <= 3
+    assert abs(np.linalg.norm(OS.to_vector(out) - y) ** 2 - sum(eps)) < 1e-12 * np.linalg.norm(y) ** 2
+
+
+def test_schmidt_spectra_match_dense_unfoldings():
+    # the Schmidt values at bond k are the singular values of the (d^k) x (d^(N-k)) unfolding of the vector
+    bonds = [1, 4, 9, 7, 3, 1]
+    sites = synth.random_mps_sites(bonds, 3, seed=904)
+    v = OS.to_vector(sites)
+    spec = OS.schmidt_spectra(sites)
+    N, d = 5, 3
+    for k in range(1, N):
+        s_ref = np.linalg.svd(v.reshape(d ** k, d ** (N - k)), compute_uv=False)
+        s = np.sort(spec[k - 1])[::-1]
+        r = len(s)
+        assert np.allclose(s, s_ref[:r], rtol=0, atol=1e-12 * s_ref[0])
+        assert np.all(s_ref[r:] < 1e-12 * s_ref[0])

@@ -64,6 +64,11 @@ def test_noalloc_matches_workspace_entry_point(lib, eng):
         assert np.abs(s1 - s0).max() <= 2e-6 * s0.max(), i
         assert abs(st1.discarded - st0.discarded) <= 1e-6 * st0.discarded + 1e-7 * n2, i
         assert np.abs(U1.conj().T @ U1 - np.eye(chi)).max() < 2e-6, i
+        # and both against the optimum of LAPACK's FP64 SVD (Eckart-Young)
+        s = np.linalg.svd(T64, compute_uv=False)
+        exact = float((s[chi:] ** 2).sum())
+        assert abs(st1.discarded - exact) <= 1e-6 * n2, i
+        assert abs(np.linalg.norm(U1 @ C1 - T64) ** 2 - exact) <= 1e-5 * n2, i
 
 
 def test_noalloc_rejects_sizes_beyond_the_scratch(lib):
