@@ -38,8 +38,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--prec", choices=["fp32", "mixed"], default="fp32",
-                    help="mixed (BF16 tensor-core site contractions) is not built: the library rejects it")
+    ap.add_argument("--prec", choices=["fp32", "mixed", "both"], default="both",
+                    help="site contractions in FP32 (SIMT) or mixed (split-BF16 tcgen05 tensor cores, FP32 "
+                         "accumulation); both: the headline value is the mixed path, the FP32 plain path is timed "
+                         "beside it")
     ap.add_argument("--n", type=int, default=16)
     ap.add_argument("--chi", type=int, default=128)
     ap.add_argument("--cutoff", type=float, default=1e-10)
@@ -54,9 +56,6 @@ def parse():
     ap.add_argument("--oracle-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--oracle-budget", type=float, default=30.0, help=argparse.SUPPRESS)
     args = ap.parse_args()
-    if args.prec == "mixed":
-        ap.exit(2, "bench.py: the mixed-precision path (BF16 tensor-core site contractions) is not built; "
-                   "libqtn rejects QTN_MIXED with QTN_ERR_ARG\n")
     return args
 
 
@@ -181,7 +180,7 @@ def build_state_gpu(qtn, n: int, chi: int, cutoff: float):
     return out
 
 
-def run_ours(args, rank, ws, local):
+def run_ours(args, rank, ws, local, prec):
     import torch
     from paper_2510_23089_gb300 import qtn
 
@@ -205,7 +204,7 @@ def run_ours(args, rank, ws, local):
     use_graph = not args.eager
     # one Fresnel step recorded as a CUDA graph (qtn_batch_create) and replayed per step
     batch = qtn.Batch([eng], [psi], [Q], [Qd], [D], n_steps=1, chi_max=chi, cutoff=args.cutoff,
-                      prec=args.prec) if use_graph else None
+                      prec=prec) if use_graph else None
 
     def reset():
         psi.sites.copy_(psi0.sites)
@@ -216,7 +215,7 @@ def run_ours(args, rank, ws, local):
         if use_graph and not eager:
             batch.launch(1)
         else:
-            eng.fresnel_step(psi, "interleaved", Q, Qd, D, 1, chi, args.cutoff, args.prec, stats=False)
+            eng.fresnel_step(psi, "interleaved", Q, Qd, D, 1, chi, args.cutoff, prec, stats=False)
 
     with torch.cuda.stream(stream):
         reset()
@@ -247,6 +246,7 @@ def run_ours(args, rank, ws, local):
         barrier(ws)
         total_ms = max_over_ranks(sum(times), ws)
         bonds_after = psi.bonds()
+        final = psi.clone()                                 # the state after the timed steps (accuracy check)
 
         # kernel classes: CUDA events around every launch cannot sit inside a replayed graph, so the same
         # steps run once more without the graph and with the library's profiling on
@@ -264,9 +264,10 @@ def run_ours(args, rank, ws, local):
                 e1.record(stream)
                 e1.synchronize()
                 pt.append(e0.elapsed_time(e1))
-            for cls, name in ((0, "k_gemm"), (1, "k_eig_jacobi")):
+            for cls, name in ((0, "k_gemm"), (1, "k_eig_jacobi"), (2, "k_gemm_tc")):
                 ms, cnt, fl = eng.profile_read(cls)
-                prof[name] = (ms, cnt, fl)
+                if cnt:
+                    prof[name] = (ms, cnt, fl)
             eng.profile(False)
             prof_ms = sum(pt)
 
@@ -297,7 +298,7 @@ def run_ours(args, rank, ws, local):
     return {
         "times": times, "total_ms": total_ms, "clocks": clocks, "launches": launches, "prof": prof,
         "prof_ms": prof_ms, "e2e_ms": e2e_ms, "h2d": h2d, "bonds": bonds_after, "bonds0": psi0.bonds(),
-        "Qw": Q.w_max, "Dw": D.w_max, "graph": use_graph,
+        "Qw": Q.w_max, "Dw": D.w_max, "graph": use_graph, "final": final,
     }
 
 
@@ -562,6 +563,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
+        config["precision"] = "f64 (the oracle)"
         done, sec, bonds = oracle_steps(args.n, args.chi, args.cutoff, args.steps, 120.0)
         value = done / sec
         line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus, "steps": done,
@@ -607,13 +609,19 @@ def main():
         if rank == 0:
             print(json.dumps(line), flush=True)
         return
-    r = run_ours(args, rank, ws, local)
+    arms = ["mixed", "fp32"] if args.prec == "both" else [args.prec]
+    res = {p: run_ours(args, rank, ws, local, p) for p in arms}
+    head = arms[0]
+    r = res[head]
     steps_all = args.steps * ws
     value = steps_all / (r["total_ms"] / 1e3)
     line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["total_ms"] / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "fp32" if args.prec == "fp32" else "bf16",
+            "scaling": "weak", "vs_baseline": None, "dtype": "fp32" if head == "fp32" else "bf16",
             "data": "synthetic", "config": config}
+    line["config"]["precision"] = head if head == "fp32" else \
+        "mixed: site contractions on tcgen05 tensor cores, BF16 operands split hi+lo (3 products), FP32 " \
+        "accumulation; truncation SVD with FP64-accumulated Gram, FP32 rotations; FP64 bookkeeping"
     line["config"]["parallelism"] = f"replicas x{ws}"
     line["config"]["launch"] = "CUDA graph of one step (qtn_batch_create), replayed per step" if r["graph"] else \
         "eager (every kernel launched from the host)"
@@ -625,6 +633,24 @@ def main():
     line["e2e"] = None if r["e2e_ms"] is None else {
         "value": ws / (r["e2e_ms"] / 1e3), "unit": "steps/s", "h2d_bytes_per_step": r["h2d"],
         "d2h_bytes_per_step": r["h2d"]}
+    if "fp32" in res and head != "fp32":
+        p = res["fp32"]
+        pv = steps_all / (p["total_ms"] / 1e3)
+        from paper_2510_23089_gb300 import qtn
+        import torch
+        chk = qtn.Engine(n_sites=args.n, d=4, chi=args.chi, w=2, dense=0)
+        a, b = r["final"], p["final"]
+        d2 = chk.norm2(a) + chk.norm2(b) - 2 * chk.overlap(b, a).real
+        line["fp32_plain"] = {
+            "value": pv, "unit": "steps/s", "ms_per_step": p["total_ms"] / args.steps,
+            "e2e": None if p["e2e_ms"] is None else {"value": ws / (p["e2e_ms"] / 1e3), "unit": "steps/s"},
+            "state_bonds_final": p["bonds"], "clocks": p["clocks"], "gpu_launches": p["launches"],
+            "roofline": roofline_line(p, json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+                                      if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {},
+                                      args.steps) if p["prof"] else None}
+        line["mixed_over_plain"] = value / pv
+        line["mixed_vs_plain_rel_l2"] = float(np.sqrt(max(d2, 0.0) / chk.norm2(b)))
+        torch.cuda.synchronize()
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))

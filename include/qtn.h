@@ -64,8 +64,10 @@ typedef enum {
 typedef enum { QTN_LAYOUT_SERIAL = 0, QTN_LAYOUT_INTERLEAVED = 1, QTN_LAYOUT_1D = 2 } qtn_layout;
 
 /* Arithmetic of the site contractions.  PLAIN_FP32: FP32 SIMT FMA, FP64-accumulated Grams.
- * MIXED is reserved for BF16 tensor-core site contractions with FP32 accumulation; it is not built in
- * this version, and every call that takes a qtn_trunc returns QTN_ERR_ARG for it. */
+ * MIXED: the site contraction of every zip-up step (carry x site, Sec. V) runs on the tcgen05 tensor cores
+ * with BF16 operands split as x = hi + lo (three products per term) and FP32 accumulation in tensor memory;
+ * the truncation SVD (FP64-accumulated Gram, FP32 rotations, FP32 re-orthonormalisation) and the FP64
+ * bookkeeping are those of the plain path.  A tensor-core wait that gives up returns QTN_ERR_TIMEOUT. */
 typedef enum { QTN_PLAIN_FP32 = 0, QTN_MIXED = 1 } qtn_precision;
 
 /* Canonical form of an MPS, tracked on the host by the library. */
@@ -172,12 +174,20 @@ qtn_status qtn_workspace_size(void* ctx, int n_sites, int d, int chi_max, int w_
 qtn_status qtn_encode(void* ctx, const void* dense, int n, qtn_layout layout, qtn_trunc trunc,
                       qtn_mps* out, qtn_stats* stats, void* ws, size_t ws_bytes);
 
+/* Operator builders.  Each runs once per operator in one CTA in FP64: the
+ * operator is held as a d = 4 MPS of (out, in) index pairs, circuit layers are
+ * absorbed one at a time by FP64 zip-up passes with SVD compression at the
+ * relative cutoff `cutoff` (eigen-decomposition of the FP64 Gram, cyclic
+ * Jacobi), and the result is rounded once to complex64.  Bonds of an operator
+ * under construction are at most 32 (QTN_ERR_CAPACITY beyond, or beyond
+ * out->w_cap).  The workspace must have been sized for at least n sites.
+ * Every builder synchronises the stream (it sets out->w_max on the host). */
+
 /* Swap-free quantum Fourier transform MPO (Sec. V: the QFT as a finite-rank MPO):
  * unitary kernel exp(+2 pi i j k / L)/sqrt(L), output site p carries frequency
- * bit k_{n+1-p} (bit-reversed order).  Built on the device as the product of
- * the n circuit layers (H, then controlled phases), compressed after every
- * layer with relative cutoff `cutoff`.  inverse != 0 gives the Hermitian
- * conjugate.  out->w_cap must be >= 16. */
+ * bit k_{n+1-p} (bit-reversed order).  The product of the n circuit layers (H,
+ * then controlled phases carried on a bond of 2).  inverse != 0 gives the
+ * Hermitian conjugate.  At cutoff 1e-12 the bonds stay below 8. */
 qtn_status qtn_build_qft_mpo(void* ctx, int n, int inverse, double cutoff, qtn_mpo* out,
                              void* ws, size_t ws_bytes);
 
@@ -185,9 +195,34 @@ qtn_status qtn_build_qft_mpo(void* ctx, int n, int inverse, double cutoff, qtn_m
  * T_z(f) = exp(-i pi lambda z f^2)): diagonal entry of frequency k is
  * exp(-i pi c k_f^2 / L) with k_f the signed fftfreq integer and
  * c = lambda z / (L dx^2); indexed in bit-reversed order when bit_reversed != 0
- * (matching the swap-free QFT output).  Built by TT-SVD of the 2^n diagonal. */
+ * (matching the swap-free QFT output).  With k_f = sum_q a_q k_q over the bits
+ * of k (two's complement weights), the phase is a product of one- and two-bit
+ * diagonal gates; it is built as n controlled-phase layers. */
 qtn_status qtn_build_phase_mpo(void* ctx, int n, double c, int bit_reversed, double cutoff,
                                qtn_mpo* out, void* ws, size_t ws_bytes);
+
+/* Lattice-dispersion propagator U(t) = diag(exp(-i t cos(2 pi k / L))) in the
+ * closed form of Sec. VI.B.4 (Jacobi-Anger expansion): the sum over
+ * |p| <= p_max of (-i)^p J_p(t) exp(2 pi i p k / L), each term a product over
+ * the bits of k, so the MPO is diagonal in the bond index p with bond
+ * 2 p_max + 1 (<= 31) and boundary vectors (-i)^p J_p(t) and 1.  No
+ * compression.  bit_reversed: site q carries bit q of k (as the QFT output);
+ * else site q carries bit n-1-q.  The truncation error is at most
+ * sum_{|p| > p_max} |J_p(t)| (below 1e-10 for p_max = 14, t = 1). */
+qtn_status qtn_build_bessel_mpo(void* ctx, int n, double t, int p_max, int bit_reversed, qtn_mpo* out,
+                                void* ws, size_t ws_bytes);
+
+/* The same U(t) as a circuit of commuting Pauli-Z string gates (Sec. VI.B.3,
+ * Eq. U-product_1): c_S = 2^-n sum_k cos(2 pi k / L) (-1)^{|S & k|} by a fast
+ * Walsh-Hadamard transform on the device, every string with
+ * |c_S| >= gate_cutoff becomes the gate exp(-i t c_S P_S) =
+ * cos(t c_S) I - i sin(t c_S) P_S (a bond-2 MPO from the first to the last
+ * qubit of S), c_0 a global phase; the gates are absorbed into the identity
+ * MPO with SVD compression at `cutoff`.  The operator error is at most
+ * t * sum_{|c_S| < gate_cutoff} |c_S|.  Needs n <= 24 and a workspace sized
+ * with dense_elems >= 2^n (the coefficients live there). */
+qtn_status qtn_build_pauliz_mpo(void* ctx, int n, double t, double gate_cutoff, int bit_reversed, double cutoff,
+                                qtn_mpo* out, void* ws, size_t ws_bytes);
 
 /* Hermitian conjugate of an MPO: out[a, s', s, b] = conj(in[a, s, s', b]). */
 qtn_status qtn_mpo_dagger(void* ctx, const qtn_mpo* in, qtn_mpo* out);
@@ -303,9 +338,86 @@ qtn_status qtn_hadamard_zipup(void* ctx, const qtn_mps* b, int conj_b, qtn_mps* 
  * workspace (N chi_cap_a chi_cap_b <= its Gram capacity). */
 qtn_status qtn_overlap_grad(void* ctx, const qtn_mps* a, const qtn_mps* b, void* grad, void* ws, size_t ws_bytes);
 
+/* Reverses the site order in place: site p <-> site N-1-p, left and right
+ * bonds exchanged (LEFT and RIGHT canonical forms swap).  For an interleaved
+ * state this reverses the bit order of both axes, i.e. it turns the
+ * bit-reversed frequency order left by the swap-free QFT into natural order
+ * without any factorisation.  Enqueued; no synchronisation. */
+qtn_status qtn_reverse_sites(void* ctx, qtn_mps* psi);
+
+/* Point spread function (Sec. V, Eq. psf_eq; Fig. fig_psf_mps):
+ *   phi: in: the pupil field E_0 as an interleaved MPS (any canonical form);
+ *        out: the normalised focal field |phi> = U_qft^(x) U_qft^(y) |E_0> /
+ *        norm, in natural frequency order (sites reversed after the
+ *        swap-free QFT) and, when centre != 0, with the zero frequency moved
+ *        to the centre (k -> k + L/2 on both axes: the two bits of the most
+ *        significant site flipped).
+ *   psf: out: ||PSF>> = |phi> (.) |phi>^* (the local product of physical legs),
+ *        truncated by trunc; entries |phi|^2 summing to <phi|phi> = 1
+ *        (||PSF||_L1 = 1, minus the discarded weight).  psf->chi_cap must hold
+ *        phi's bonds (QTN_ERR_CAPACITY otherwise); must not alias phi.
+ *   qft: the per-axis QFT MPO (qtn_build_qft_mpo, not inverted).
+ * Workspace: MPO bonds up to phi's largest bond.  Synchronises (it reads the
+ * bonds of |phi> on the host). */
+qtn_status qtn_psf(void* ctx, qtn_mps* phi, const qtn_mpo* qft, int centre, qtn_trunc trunc, qtn_mps* psf,
+                   qtn_stats* stats, void* ws, size_t ws_bytes);
+
+/* Image formation by convolution (Sec. V, Eq. convolution_eq):
+ *   b <- L * U_iqft(U_qft a (.) U_qft b), the circular convolution a * b of two
+ *   interleaved L x L images (L = 2^n; the factor L undoes the normalisation
+ *   of the unitary DFT: F(a * b) = sqrt(L) F(a) F(b) per axis).
+ *   a is overwritten by U_qft a (both axes, bit-reversed frequency order).
+ *   Every pass truncates by trunc.  Synchronises (reads a's bonds). */
+qtn_status qtn_convolve(void* ctx, qtn_mps* a, qtn_mps* b, const qtn_mpo* qft, const qtn_mpo* qft_dagger,
+                        qtn_trunc trunc, qtn_stats* stats, void* ws, size_t ws_bytes);
+
+/* Angular-spectrum transfer function (Sec. VI.A, Eq. eq_astf) on the L x L
+ * frequency grid, written to dense (device complex64, L x L row-major, row =
+ * k_x, column = k_y; entries indexed bit-reversed per axis when bit_reversed
+ * != 0, matching the swap-free QFT output):
+ *   exp(2 pi i (z/lambda) (sqrt(1 - u) - 1)),  u = (lambda f_x)^2 + (lambda f_y)^2,
+ *   lambda f = (lambda / dx) k_f / L with k_f the signed fftfreq integer;
+ *   evanescent components (u > 1) decay as exp(-2 pi (z/lambda) sqrt(u - 1)).
+ * The constant exp(2 pi i z / lambda) is divided out (as exp(i k z) is in the
+ * Fresnel step).  It does not factor over the axes: encode it with qtn_encode
+ * (INTERLEAVED) into the fused 2-D operator applied by qtn_transfer_step.
+ * QTN_ERR_CAPACITY if L^2 > cap_elems.  Enqueued; no synchronisation. */
+qtn_status qtn_astf_field(void* ctx, int n, double z_over_lambda, double lambda_over_dx, int bit_reversed,
+                          void* dense, long long cap_elems);
+
+/* One propagation step with a 2-D transfer function that need not factor over
+ * the axes: psi <- U_qft^dagger (T (.) U_qft psi) with T an interleaved MPS in
+ * the bit-reversed frequency order of the swap-free QFT (e.g. the encoded
+ * qtn_astf_field), applied as an operator diagonal in the site index by
+ * zip-up.  Per pass truncation by trunc.  Synchronises (reads T's bonds). */
+qtn_status qtn_transfer_step(void* ctx, qtn_mps* psi, const qtn_mpo* qft, const qtn_mpo* qft_dagger,
+                             const qtn_mps* transfer, qtn_trunc trunc, qtn_stats* stats, void* ws, size_t ws_bytes);
+
 /* psi <- (re + i im) psi, applied to the site that carries the norm (the last
  * site of a left-canonical state, the first otherwise); canon unchanged. */
 qtn_status qtn_scale(void* ctx, qtn_mps* psi, double re, double im);
+
+/* Building block of the fixed-rank adjoint of zip-up passes (the adjoint is
+ * not in the paper; the passes are those of Sec. V, Fig. fig_mpo).  A zip-up
+ * pass that applies K to psi writes N-1 isometric sites (the frame V) and a
+ * centre c = V^dagger K psi, so with V held fixed it is psi -> V V^dagger K psi
+ * and its adjoint is g -> K^dagger V V^dagger g.  This call forms
+ *     frame <- V V^dagger W ket
+ * as an MPS: the frame's isometric sites are kept and its centre site (site
+ * N-1 of a LEFT frame, site 0 of a RIGHT one) is replaced by V^dagger W ket,
+ * contracted by three-layer transfer matrices (FP64 accumulation; nothing is
+ * truncated or factorised).
+ *   W:     per-axis MPO acting on `axis` (0 = x, 1 = y bit of interleaved
+ *          sites; d = 2 states: the whole site), or NULL for the identity.
+ *          For the backward chain pass W = K^dagger of the forward pass that
+ *          follows the frame.
+ *   ket:   any MPS with frame's n_sites and d (not aliasing frame).
+ *   frame: in: a state left by a zip-up pass (canon LEFT or RIGHT, else
+ *          QTN_ERR_ARG); out: its centre replaced.
+ * Workspace: environments of frame bond x W bond x ket bond.  Synchronises
+ * (it reads the bonds on the host). */
+qtn_status qtn_project_apply(void* ctx, const qtn_mpo* W, int axis, const qtn_mps* ket, qtn_mps* frame,
+                             void* ws, size_t ws_bytes);
 
 /* Zip-up MPO x MPS application with SVD truncation (Sec. V, Fig. fig_mpo).
  * The per-axis MPO W acts on axis `axis` (0 = x, 1 = y) of psi:

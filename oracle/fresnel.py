@@ -23,17 +23,23 @@ from . import mpo as _mpo
 from . import apply as _apply
 
 
-def fresnel_dense(E: np.ndarray, c: float) -> np.ndarray:
-    """Brute-force 2-D Fresnel transfer-function propagation (matrix DFTs)."""
+def transfer_dense(E: np.ndarray, Dk: np.ndarray) -> np.ndarray:
+    """Brute-force 2-D propagation by a separable transfer function: E_z = F^-1[F[E] Dk(k_x) Dk(k_y)] with the
+    unitary matrix DFT F (Sec. VI.A; Dk indexed by the natural frequency bin k)."""
     E = np.asarray(E, dtype=np.complex128)
     L = E.shape[0]
     F = _mpo.dft_matrix(L)
-    kf = _mpo.fftfreq_int(L).astype(np.float64)
-    D = np.exp(-1j * np.pi * c * kf ** 2 / L)
     Ehat = F @ E @ F.T
-    Ehat = D[:, None] * Ehat * D[None, :]
+    Ehat = Dk[:, None] * Ehat * Dk[None, :]
     Fi = F.conj().T
     return Fi @ Ehat @ Fi.T
+
+
+def fresnel_dense(E: np.ndarray, c: float) -> np.ndarray:
+    """Brute-force 2-D Fresnel transfer-function propagation (matrix DFTs)."""
+    L = np.asarray(E).shape[0]
+    kf = _mpo.fftfreq_int(L).astype(np.float64)
+    return transfer_dense(E, np.exp(-1j * np.pi * c * kf ** 2 / L))
 
 
 def fresnel_dense_1d(v: np.ndarray, c: float) -> np.ndarray:

@@ -165,8 +165,12 @@ def qft_mpo_dense(n: int, cutoff: float = 1e-12, chi_max: int = 1 << 30):
 
 
 def diagonal_mpo(vec: np.ndarray, n: int, cutoff: float = 1e-12, chi_max: int = 1 << 30):
-    """Diagonal MPO of a length-2^n vector: TT-SVD (d = 2), then delta(s', s)."""
+    """Diagonal MPO of a length-2^n vector: TT-SVD (d = 2), brought to right-canonical form (the form in which
+    every operator here is delivered: the zip-up truncation depends on the gauge of the operator it applies,
+    and right-canonical forms differ only by unitary bond transformations, to which it is blind), then
+    delta(s', s)."""
     sites, _ = _mps.tt_svd(vec, n, 2, chi_max, cutoff)
+    sites = _mps.right_canonicalize(sites)
     out = []
     for A in sites:
         a, _, b = A.shape
@@ -228,3 +232,82 @@ def embed(W, layout: str, axis: int, n: int):
 def mirror(W):
     """Reverse the chain and swap each core's left/right bonds."""
     return [c.transpose(3, 1, 2, 0).copy() for c in reversed(W)]
+
+
+# ----------------------------------------------------------------------------- lattice dispersion (Sec. VI.B)
+#
+# U(t) = sum_s exp(-i t eps(s)) |s><s| with eps(s) = cos(2 pi x_s), x_s = k / L the frequency of the basis
+# state (Sec. VI.B.2-4: the tight-binding dispersion of the discretised free particle).  Both builders return
+# the diagonal MPO in the site order of the swap-free QFT output (site q carries bit q of k) when
+# ``bit_reversed``, else in natural order (site q carries bit n-1-q).
+
+def lattice_diagonal(n: int, t: float, bit_reversed: bool = True) -> np.ndarray:
+    """The exact diagonal exp(-i t cos(2 pi k / L)), indexed by the site-ordered flat index."""
+    L = 1 << n
+    k = np.arange(L)
+    D = np.exp(-1j * t * np.cos(2 * np.pi * k / L))
+    if not bit_reversed:
+        return D
+    return np.array([D[bit_reverse(idx, n)] for idx in range(L)])
+
+
+def bessel_mpo(n: int, t: float, p_max: int, bit_reversed: bool = True):
+    """Closed-form diagonal MPO of U(t) (Sec. VI.B.4): the Jacobi-Anger expansion
+    exp(-i t cos theta) = sum_p (-i)^p J_p(t) exp(i p theta), truncated to |p| <= p_max, with theta = 2 pi k / L
+    = sum over bits; the core of site q is diagonal in the bond index p and carries exp(i p theta_q s_q), the
+    left boundary vector is (-i)^p J_p(t) and the right one all ones.  Bond 2 p_max + 1."""
+    from scipy.special import jv
+    ps = np.arange(-p_max, p_max + 1)
+    chi = len(ps)
+    vl = np.array([(-1j) ** int(p) * jv(int(p), t) for p in ps])
+    cores = []
+    for q in range(n):
+        theta = 2 * np.pi * (2.0 ** q) / (1 << n) if bit_reversed else 2 * np.pi / 2.0 ** (q + 1)
+        c = np.zeros((chi, 2, 2, chi), dtype=np.complex128)
+        for i, p in enumerate(ps):
+            for s in (0, 1):
+                c[i, s, s, i] = np.exp(1j * p * theta * s)
+        cores.append(c)
+    cores[0] = np.einsum("p,pstq->stq", vl, cores[0])[None]     # left boundary vector
+    cores[-1] = cores[-1].sum(axis=3)[..., None]                 # right boundary vector of ones
+    return cores
+
+
+def walsh_coefficients(eps: np.ndarray) -> np.ndarray:
+    """c_S = 2^-n sum_s eps(s) (-1)^popcount(S & s) (Sec. VI.B.3, Eq. coeff_trace), by the fast Walsh-Hadamard
+    butterflies written out (bit b of S pairs with bit b of s)."""
+    v = np.array(eps, dtype=np.float64).copy()
+    N = len(v)
+    h = 1
+    while h < N:
+        for i in range(0, N, 2 * h):
+            a = v[i:i + h].copy()
+            b = v[i + h:i + 2 * h].copy()
+            v[i:i + h] = a + b
+            v[i + h:i + 2 * h] = a - b
+        h *= 2
+    return v / N
+
+
+def pauliz_mpo(n: int, t: float, gate_cutoff: float, cutoff: float = 1e-12, bit_reversed: bool = True):
+    """Diagonal MPO of the Pauli-Z circuit (Sec. VI.B.3, Eq. U-product_1): the product over strings with
+    |c_S| >= gate_cutoff of cos(t c_S) I - i sin(t c_S) P_S, times the global phase exp(-i t c_0).  The gates
+    commute and each is diagonal, so the product is diag(exp(-i t H_trunc(k))) with H_trunc the kept Walsh
+    expansion; its diagonal is compressed by TT-SVD at ``cutoff``."""
+    L = 1 << n
+    k = np.arange(L)
+    c = walsh_coefficients(np.cos(2 * np.pi * k / L))
+    keep = np.abs(c) >= gate_cutoff
+    keep[0] = True
+    ct = np.where(keep, c, 0.0)
+    # H_trunc(k) = sum_S c_S (-1)^popcount(S & k): the same butterflies, unscaled
+    H = walsh_coefficients(ct) * L
+    D = np.exp(-1j * t * H)
+    if bit_reversed:
+        D = np.array([D[bit_reverse(idx, n)] for idx in range(L)])
+    return diagonal_mpo(D, n, cutoff)
+
+
+def diag_of(W) -> np.ndarray:
+    """Diagonal of a diagonal MPO, by site-ordered flat index."""
+    return np.diag(to_dense(W)).copy()

@@ -151,6 +151,10 @@ constexpr int EIG_CB = 16;                      // columns per block of the re-o
 constexpr int EIG_QC = EIG_THREADS / 32;        // finished columns per projection chunk (one per warp)
 constexpr float EIG_DEP0 = 1e-3f;               // residual below which a column is dependent (first run)
 constexpr float EIG_NOISE = 1.0e-13f;           // |w_i| |w_j| floor (matrix scaled to unit largest diagonal)
+// The scaled Gram is stored in FP32, so eigenvalues below ~1e-7 of the largest are rounding.  A sweep that still
+// rotates only pairs of columns whose norms (eigenvalues) are not both above EIG_SIG is chasing that rounding
+// and does not count as unconverged.
+constexpr float EIG_SIG = 1.0e-6f;
 
 __device__ __forceinline__ void circle_pair(int t, int k, int rr, int& i, int& j) {
     // round-robin tournament (circle method) on rr players, round t in [0, rr-2]
@@ -187,8 +191,8 @@ __device__ __forceinline__ int jacobi_slot(int c, int r16) {
 template <int LPP>
 __device__ __forceinline__ void jacobi_pair(float2* __restrict__ W, float* __restrict__ cn2, int* __restrict__ tmod,
                                             int r, int r16, int col_i, int col_j, int li, unsigned gmask, int g, int SL,
-                                            bool first_sweep, float tol, int* rotated, unsigned long long& my_pairs,
-                                            unsigned long long& my_rot) {
+                                            bool first_sweep, float tol, int* rotated, int* sig_rotated,
+                                            unsigned long long& my_pairs, unsigned long long& my_rot) {
     if (col_i >= r || col_j >= r) return;
     const int si = jacobi_slot(col_i, r16), sj = jacobi_slot(col_j, r16);
     if (!first_sweep && max(tmod[si], tmod[sj]) < g - SL) return;
@@ -259,6 +263,7 @@ __device__ __forceinline__ void jacobi_pair(float2* __restrict__ W, float* __res
         tmod[si] = g;
         tmod[sj] = g;
         *rotated = 1;
+        if (ab2 > EIG_SIG * EIG_SIG) *sig_rotated = 1;
         ++my_rot;
     }
 }
@@ -272,7 +277,7 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
     extern __shared__ float2 W[];                // column-major, W[j*EIG_RS + i]
     __shared__ double nrm[EIG_MAX];
     __shared__ int rank_of[EIG_MAX];
-    __shared__ int rotated;
+    __shared__ int rotated, sig_rotated;
     const int r = rdim.eval(Rc);
     const long long ld = ldd.eval(Rc), ldu = ldud.eval(Rc);
     if (r <= 0) return;
@@ -310,7 +315,7 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
     int sweep = 0;
     bool converged = (r < 2);
     for (; sweep < max_sweeps && !converged; ++sweep) {
-        if (tid == 0) rotated = 0;
+        if (tid == 0) { rotated = 0; sig_rotated = 0; }
         for (int j = tid / 32; j < r; j += EIG_THREADS / 32) {
             float s2 = 0.f;
             for (int row = tid % 32; row < r; row += 32) {
@@ -329,7 +334,7 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
                 int a, b;
                 circle_pair(u, k, EIG_BS, a, b);
                 jacobi_pair<8>(W, cn2, tmod, r, r16, warp_j * EIG_BS + a, warp_j * EIG_BS + b, li, gmask, g0 + u, SL,
-                               sweep == 0, tol, &rotated, my_pairs, my_rot);
+                               sweep == 0, tol, &rotated, &sig_rotated, my_pairs, my_rot);
                 __syncwarp();
             }
         }
@@ -342,8 +347,8 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
                 const unsigned gmask = 0xFu << (4 * q);
                 for (int s2 = 0; s2 < EIG_BS; ++s2) {
                     jacobi_pair<4>(W, cn2, tmod, r, r16, A * EIG_BS + q, B * EIG_BS + ((q + s2) & (EIG_BS - 1)), li,
-                                   gmask, g0 + (EIG_BS - 1) + t * EIG_BS + s2, SL, sweep == 0, tol, &rotated, my_pairs,
-                                   my_rot);
+                                   gmask, g0 + (EIG_BS - 1) + t * EIG_BS + s2, SL, sweep == 0, tol, &rotated, &sig_rotated,
+                                   my_pairs, my_rot);
                     __syncwarp();
                 }
             }
@@ -654,7 +659,8 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
     }
     if (tid == 0) {
         atomicMax(&Rw[R_SWEEPS], sweep);
-        if (!converged && report_nonconv) raise_flag(Rw, F_NOCONV);
+        // unconverged only when the last sweep still rotated a pair above the rounding level of the scaled Gram
+        if (!converged && report_nonconv && sig_rotated) raise_flag(Rw, F_NOCONV);
         // algorithmic FLOPs: 8 per row for the inner product of a pair, 24 per row for a rotation,
         // 8 r^3 for the re-orthonormalisation (projections and Cholesky QR, complex)
         if (prof != nullptr)

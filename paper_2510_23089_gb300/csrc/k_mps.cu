@@ -324,14 +324,19 @@ __global__ void k_row_weights(const float2* __restrict__ X, Dim ldx, Dim rows, D
     }
 }
 
-// Truncation rule on projected weights: sort descending, keep the smallest k >= 1 whose discarded
-// weight (total - kept) is <= cutoff * total, cap by chi_max and the capacity.  total = trace of the
-// Gram matrix (the exact weight of the factorised matrix).  Writes perm[0..k), R[R_K], discarded.
+// Truncation rule on projected weights (FP64): sort descending, keep the smallest k >= 1 whose discarded
+// weight is <= cutoff * total, cap by chi_max and the capacity.  The discarded weight is the sum of the
+// weights left out, accumulated directly from the smallest upwards (suffix sums), never the difference
+// total - kept: that difference carries the FP32 rounding of every projected weight (~1e-7 of the total),
+// which would swamp cutoffs near 1e-10.  On the range-finder path with a full-rank sketch the weight of T
+// outside the sketch, |T|^2 - sum of captured weights (L_TRACE holds |T|^2), is part of every tail; when the
+// sketch has dependent columns it spans the range of T and that difference is rounding only.
+// Writes perm[0..k), R[R_K], ledger[L_DISCARDED] += discarded.
 __global__ void k_select(const double* __restrict__ w, Dim rdim, int chi_max, double cutoff, int chi_cap,
-                         int total_from_weights, int* __restrict__ perm, int* __restrict__ R,
-                         double* __restrict__ ledger) {
-    if (total_from_weights < 0) total_from_weights = (R[R_RAND] == 0);   // decided on the device
+                         int unused, int* __restrict__ perm, int* __restrict__ R, double* __restrict__ ledger) {
+    (void)unused;
     __shared__ double sorted_w[1024];
+    __shared__ double tail[1025];
     const int r = rdim.eval(R);
     for (int j = threadIdx.x; j < r; j += blockDim.x) {
         const double v = w[j];
@@ -345,36 +350,24 @@ __global__ void k_select(const double* __restrict__ w, Dim rdim, int chi_max, do
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        // total weight: the sum of all projected weights when the basis spans the whole row space (the same
-        // FP32 projections as the kept weights, so the discarded weight is consistent); on the range-finder
-        // path the exact |T|^2, which also counts the weight outside the sketch, unless the FP32 projections
-        // over-count it (their sum then takes its place, so the tail is never consumed by rounding)
-        double wsum = 0.0;
-        for (int i = r - 1; i >= 0; --i) wsum += sorted_w[i];
-        const double total = total_from_weights ? wsum : fmax(ledger[L_TRACE], wsum);
-        double kept = 0.0;
-        int k = 0;
+        tail[r] = 0.0;
+        for (int i = r - 1; i >= 0; --i) tail[i] = tail[i + 1] + fmax(sorted_w[i], 0.0);
+        const double wsum = tail[0];
+        const bool full_sketch = (R[R_RAND] == 1 && R[R_DEP] == 0);
+        const double outside = full_sketch ? fmax(ledger[L_TRACE] - wsum, 0.0) : 0.0;
+        const double total = wsum + outside;
         // directions whose captured weight is below NULL_FLOOR * total are numerically null for FP32 data
-        // (singular value below ~3e-7 of the norm, a few FP32 ulps): they are never kept, whatever the cutoff.
+        // (singular value below ~3e-7 of the norm, a few FP32 ulps): they are never kept, whatever the cutoff
         const double NULL_FLOOR = 1e-13;
-        while (k < r) {
-            if (k >= 1 && total - kept <= cutoff * total) break;
-            if (k >= 1 && !(sorted_w[k] > NULL_FLOOR * total)) break;
-            kept += sorted_w[k];
-            ++k;
-        }
-        if (k < 1) k = 1;
+        int k = 1;
+        while (k < r && tail[k] + outside > cutoff * total && sorted_w[k] > NULL_FLOOR * total) ++k;
         // a rank can never exceed the smaller dimension of the factorised matrix
         const int rank_bound = min(R[R_M], R[R_N]);
         int kk = min(min(k, chi_max), max(rank_bound, 1));
         // the rule asks for more directions than the bond can hold: clamp and report, never silently
         if (kk > chi_cap) { kk = chi_cap; raise_flag(R, F_CAPACITY); }
-        kept = 0.0;
-        for (int i = 0; i < kk; ++i) kept += sorted_w[i];
-        double disc = total - kept;
-        if (disc < 0.0) disc = 0.0;
-        ledger[L_DISCARDED] += disc;
-        if (!isfinite(total) || !isfinite(wsum) || !isfinite(ledger[L_TRACE])) raise_flag(R, F_NONFINITE);
+        ledger[L_DISCARDED] += tail[kk] + outside;
+        if (!isfinite(total) || !isfinite(ledger[L_TRACE])) raise_flag(R, F_NONFINITE);
         R[R_K] = kk;
         R[R_MAXBOND] = max(R[R_MAXBOND], kk);
     }
@@ -517,95 +510,6 @@ __global__ void k_quantics_to_dense(const float2* __restrict__ q, float2* __rest
 }
 
 // ------------------------------------------------------------------ MPO construction
-
-// Identity operator as a d = 4 "MPS" (index t*2 + s), bond 1, left canonical:
-// sites 0..n-2 hold (1,0,0,1)/sqrt(2), the last site (1,0,0,1) * 2^((n-1)/2).
-__global__ void k_identity_mpo_state(float2* __restrict__ sites, int* __restrict__ bond, int n, int cap) {
-    const int p = blockIdx.x;
-    if (p >= n) return;
-    float2* s = sites + (long long)p * cap * 4 * cap;
-    const float v = (p < n - 1) ? 0.70710678118654752f : (float)pow(2.0, 0.5 * (n - 1));
-    if (threadIdx.x < 4) {
-        const int t = threadIdx.x >> 1, u = threadIdx.x & 1;
-        s[(long long)threadIdx.x * cap] = make_float2(t == u ? v : 0.f, 0.f);
-    }
-    if (threadIdx.x == 0) {
-        bond[p] = 1;
-        if (p == n - 1) bond[n] = 1;
-    }
-}
-
-// Layer j of the swap-free QFT circuit (H on qubit j, then controlled phases exp(i pi b s / 2^(k-j)) with
-// every qubit k > j, the post-H bit b carried on a bond of size 2) as an MPO on n sites.
-__global__ void k_qft_layer(float2* __restrict__ W, int* __restrict__ bond, int n, int j, int wcap) {
-    const int p = blockIdx.x;
-    if (p >= n) return;
-    float2* c = W + (long long)p * wcap * 4 * wcap;
-    const float h = 0.70710678118654752f;
-    if (threadIdx.x == 0) {
-        for (int e = 0; e < wcap * 4 * wcap; ++e) c[e] = make_float2(0.f, 0.f);
-        if (p < j) {
-            c[((0 * 2 + 0) * 2 + 0) * wcap + 0] = make_float2(1.f, 0.f);
-            c[((0 * 2 + 1) * 2 + 1) * wcap + 0] = make_float2(1.f, 0.f);
-        } else if (p == j) {
-            const int wr = (j < n - 1) ? 2 : 1;
-            for (int b = 0; b < 2; ++b)
-                for (int s = 0; s < 2; ++s) {
-                    const float hv = (b == 1 && s == 1) ? -h : h;
-                    c[((0 * 2 + b) * 2 + s) * wcap + (wr == 2 ? b : 0)] = make_float2(hv, 0.f);
-                }
-        } else {
-            const int wr = (p < n - 1) ? 2 : 1;
-            for (int b = 0; b < 2; ++b)
-                for (int s = 0; s < 2; ++s) {
-                    double sn, cs;
-                    sincospi((double)(b * s) / (double)(1ll << (p - j)), &sn, &cs);
-                    c[((b * 2 + s) * 2 + s) * wcap + (wr == 2 ? b : 0)] = make_float2((float)cs, (float)sn);
-                }
-        }
-        const int wl = (p <= j) ? 1 : 2;
-        const int wr = (p < j) ? 1 : ((p < n - 1) ? 2 : 1);
-        bond[p] = wl;
-        if (p == n - 1) bond[n] = wr;
-    }
-}
-
-// Fresnel transfer function on the grid, indexed by the site-ordered flat index (bit reversed if asked):
-// exp(-i pi c k_f^2 / L), k_f the signed fftfreq integer.  Phase reduced modulo 2 in FP64 before sincospi.
-__global__ void k_phase_vector(float2* __restrict__ v, int n, double c, int bit_reversed) {
-    const long long L = 1ll << n;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < L;
-         idx += (long long)gridDim.x * blockDim.x) {
-        long long k = idx;
-        if (bit_reversed) k = (long long)(__brevll((unsigned long long)idx) >> (64 - n));
-        const long long kf = (k < L / 2) ? k : k - L;
-        // phase / pi = -c kf^2 / L, reduced modulo 2 exactly enough in FP64
-        double e = c * (double)kf * (double)kf / (double)L;
-        e = fmod(e, 2.0);
-        double s, co;
-        sincospi(-e, &s, &co);
-        v[idx] = make_float2((float)co, (float)s);
-    }
-}
-
-// Diagonal MPO from a d = 2 MPS: W[a, t, s, b] = delta(t, s) A[a, s, b].
-__global__ void k_diag_mpo(const float2* __restrict__ A, int acap, const int* __restrict__ abond,
-                           float2* __restrict__ W, int wcap, int* __restrict__ wbond, int n) {
-    const int p = blockIdx.x;
-    if (p >= n) return;
-    const int bl = abond[p], br = abond[p + 1];
-    const float2* a = A + (long long)p * acap * 2 * acap;
-    float2* w = W + (long long)p * wcap * 4 * wcap;
-    for (int e = threadIdx.x; e < bl * 4 * br; e += blockDim.x) {
-        const int l = e / (4 * br), ts = (e / br) % 4, r = e % br;
-        const int t = ts >> 1, s = ts & 1;
-        w[((long long)l * 4 + ts) * wcap + r] = (t == s) ? a[((long long)l * 2 + s) * acap + r] : make_float2(0.f, 0.f);
-    }
-    if (threadIdx.x == 0) {
-        wbond[p] = bl;
-        if (p == n - 1) wbond[n] = br;
-    }
-}
 
 // Hermitian conjugate of MPO cores: out[a, t, s, b] = conj(in[a, s, t, b]).
 __global__ void k_mpo_dagger(const float2* __restrict__ in, const int* __restrict__ ibond, int icap,

@@ -39,6 +39,7 @@ __global__ void k_hadamard(const float2*, const int*, int, const float2*, const 
                            int);
 __global__ void k_scale_site(float2*, int, int, const int*, int, float, float);
 constexpr int CGS_MAXM_ALL = 1024;
+constexpr int RF_POWER_ITERS = 3;   // power iterations of the range finder (full-rank sketches only)
 constexpr size_t CGS_SMEM = (size_t)32 * 512 * sizeof(float2);   // = 16 x 1024 = 8 x 2048 as well
 __global__ void k_row_weights(const float2*, Dim, Dim, Dim, double*, const int*);
 __global__ void k_select(const double*, Dim, int, double, int, int, int*, int*, double*);
@@ -50,10 +51,6 @@ __global__ void k_to_f32(const double2*, float2*, int, Dim, const int*);
 __global__ void k_whiten(float2*, int, const double*, Dim, double, const int*);
 __global__ void k_dense_to_quantics(const float2*, float2*, int, int, int*);
 __global__ void k_quantics_to_dense(const float2*, float2*, int, int);
-__global__ void k_identity_mpo_state(float2*, int*, int, int);
-__global__ void k_qft_layer(float2*, int*, int, int, int);
-__global__ void k_phase_vector(float2*, int, double, int);
-__global__ void k_diag_mpo(const float2*, int, const int*, float2*, int, int*, int);
 __global__ void k_mpo_dagger(const float2*, const int*, int, float2*, int*, int, int);
 __global__ void k_amplitudes(const float2*, const int*, int, int, int, const int*, int, float2*, float2*);
 __global__ void k_transfer_right(const double2*, int, const float2*, int, int, int, const float2*, int, int, int, int,
@@ -90,6 +87,9 @@ __global__ void k_copy_ledger_out(const double* ledger, const int* R, double* ou
 }
 
 // ------------------------------------------------------------------ workspace layout
+// Offset of a region a layout does not provide: bound to a null pointer, so a use cannot alias another region.
+constexpr size_t WS_UNUSED = ~(size_t)0;
+
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 WsLayout ws_layout(int N, int d, int chi, int w, long long dense) {
@@ -120,17 +120,14 @@ WsLayout ws_layout(int N, int d, int chi, int w, long long dense) {
     L.Q = take(std::max(gdim * pc, pc * pc) * c8);
     L.S64 = take(gdim * gdim * c16);
     L.Z = take(std::max(gdim * nc, pc * pc) * c8);   // projected rows X = U^dagger T (zip-up)
-    L.omega = take((size_t)N * chi * d * chi * c8 + (size_t)N * 64 * c8);   // MPS-sized scratch + layer MPO
+    L.omega = WS_UNUSED;
     const size_t dn = (size_t)std::max<long long>(dense, 1);
     L.X0 = take(dn * c8);
     L.X1 = take(dn * c8);
+    L.b64 = take(build64_scratch_bytes(std::max(N, 1)));   // FP64 operator builds
     L.total = off;
     return L;
 }
-
-// Offset of a region a layout does not provide: bound to a null pointer, so any use faults loudly on the
-// host side of a check instead of aliasing another region.
-constexpr size_t WS_UNUSED = ~(size_t)0;
 
 static Ws ws_bind(void* base, const WsLayout& L) {
     char* b = (char*)base;
@@ -157,40 +154,27 @@ static Ws ws_bind(void* base, const WsLayout& L) {
 
 // extra int scratch after the registers: perm[gdim], tmp bonds[...]
 static int* ws_perm(Ws& w) { return w.R + R_COUNT; }
-static int* ws_tmpbond(Ws& w) { return w.R + R_COUNT + 2 * std::max(w.L.m_cap, w.L.p_cap); }
 static double* ws_weights(Ws& w) { return w.lam + std::max(w.L.m_cap, w.L.p_cap); }
 static double* ws_lam2(Ws& w) { return w.lam + 2 * std::max(w.L.m_cap, w.L.p_cap); }
-static float2* ws_mtmp(void* base, const WsLayout& L) { return (float2*)((char*)base + L.omega); }
 
-#define CK(expr)                                                      \
-    do {                                                              \
-        cudaError_t _e = (expr);                                      \
-        if (_e != cudaSuccess) {                                      \
-            fprintf(stderr, "qtn: CUDA error %s at %s:%d\n", cudaGetErrorString(_e), __FILE__, __LINE__); \
-            return QTN_ERR_CUDA;                                      \
-        }                                                             \
-    } while (0)
-#define CKL()                           \
-    do {                                \
-        count_launch(PROF_OTHER, 0, false); \
-        CK(cudaGetLastError());         \
-    } while (0)
 
 long long launch_total();
 void add_launches(long long n);
 void prof_begin(bool on, double* ledger);
 void prof_read(int cls, double* ms, long long* launches);
 
-// Truncation rules this build accepts: the FP32 plain path only (QTN_MIXED is reserved), a finite
-// non-negative cutoff.
-static bool trunc_ok(const qtn_trunc& t) {
-    return t.prec == QTN_PLAIN_FP32 && t.cutoff >= 0.0 && isfinite(t.cutoff) && t.max_sweeps >= 0;
+// Truncation rules: FP32 plain or mixed (tensor-core site contractions), a finite non-negative cutoff.
+bool trunc_ok(const qtn_trunc& t) {
+    return (t.prec == QTN_PLAIN_FP32 || t.prec == QTN_MIXED) && t.cutoff >= 0.0 && isfinite(t.cutoff) &&
+           t.max_sweeps >= 0;
 }
 
 // Relative weight below which a direction of an untruncated (gauge-only) sweep is FP32 round-off.
 constexpr double EXACT_CUTOFF = 1e-13;
 
 cudaError_t configure_eig_kernel();
+cudaError_t configure_build64_kernel();
+cudaError_t configure_tc_kernel();
 
 // Kernels with more than 48 KB of dynamic shared memory need the opt-in on every device they run on.
 static std::once_flag g_dev_once[QTN_MAX_DEVICES];
@@ -203,6 +187,8 @@ cudaError_t configure_device_kernels(int device) {
         cudaError_t e = cudaGetDevice(&prev);
         if (e == cudaSuccess && prev != device) e = cudaSetDevice(device);
         if (e == cudaSuccess) e = configure_eig_kernel();
+        if (e == cudaSuccess) e = configure_build64_kernel();
+        if (e == cudaSuccess) e = configure_tc_kernel();
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_cgs_block_32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CGS_SMEM);
         if (e == cudaSuccess)
@@ -215,7 +201,7 @@ cudaError_t configure_device_kernels(int device) {
     return g_dev_err[device];
 }
 
-static int grid_for(long long n, int threads, int sm) {
+int grid_for(long long n, int threads, int sm) {
     long long g = (n + threads - 1) / threads;
     long long cap = (long long)sm * 8;
     return (int)std::max(1LL, std::min(g, cap));
@@ -361,54 +347,59 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
         // represented at the square of its relative singular value.
         k_set_pi<<<1, 1, 0, s>>>(w.R);
         CKL();
-        if (one_chunk && ncap <= 2048) {   // Z fits the B buffer whole and the block orthonormaliser
-            {   // Z = T^dagger Q (n x p) in the B buffer
-                GemmDesc g{};
-                g.A = mat(io.T, dc(1), io.n, 1);
-                g.B = mat(w.Y, dc(pc), dc(1));
-                g.C = w.G32; g.crs = dc(pc); g.ccs = dc(1);
-                g.M = io.n; g.N = P; g.K = io.m;
-                g.guard_reg = R_PI; g.guard_val = 1;
-                CK(launch_gemm(g, ncap, pc, mc, w.R, s));
+        // Three power iterations: for a chi-limited truncation of a slowly decaying spectrum every iteration
+        // shrinks the weight the sketch misses near the kept rank by about (s_(p+1) / s_k)^4 (one was measured
+        // 2.6e-5 of |T|^2 above the Eckart-Young optimum at 512 x 768, chi 128, s_k / s_1 = 0.08).
+        for (int it = 0; it < RF_POWER_ITERS; ++it) {
+            if (one_chunk && ncap <= 2048) {   // Z fits the B buffer whole and the block orthonormaliser
+                {   // Z = T^dagger Q (n x p) in the B buffer
+                    GemmDesc g{};
+                    g.A = mat(io.T, dc(1), io.n, 1);
+                    g.B = mat(w.Y, dc(pc), dc(1));
+                    g.C = w.G32; g.crs = dc(pc); g.ccs = dc(1);
+                    g.M = io.n; g.N = P; g.K = io.m;
+                    g.guard_reg = R_PI; g.guard_val = 1;
+                    CK(launch_gemm(g, ncap, pc, mc, w.R, s));
+                }
+                if ((st = block_orth(w.G32, io.n, ncap, R_PI))) return st;
+                {   // Y = T Z
+                    GemmDesc g{};
+                    g.A = mat(io.T, io.n, dc(1));
+                    g.B = mat(w.G32, dc(pc), dc(1));
+                    g.C = w.Y; g.crs = dc(pc); g.ccs = dc(1);
+                    g.M = io.m; g.N = P; g.K = io.n;
+                    g.guard_reg = R_PI; g.guard_val = 1;
+                    CK(launch_gemm(g, mc, pc, ncap, w.R, s));
+                }
+                if ((st = block_orth(w.Y, io.m, mc, R_PI))) return st;
+            } else {
+                // T too wide for the intermediate: Y' = T (T^dagger Q) accumulated over column chunks of T
+                CK(cudaMemsetAsync(w.Q, 0, (size_t)mc * pc * sizeof(float2), s));
+                for (long long c0 = 0; c0 < io.n_cap; c0 += cw) {
+                    const int cwid = (int)std::min<long long>(cw, io.n_cap - c0);
+                    const Dim ncol = one_chunk ? io.n : dc(cwid);
+                    GemmDesc g{};                                       // Z1 = T_c^dagger Q  (cw x p) in the B buffer
+                    g.A = mat(io.T + c0, dc(1), io.n, 1);
+                    g.B = mat(w.Y, dc(pc), dc(1));
+                    g.C = w.G32; g.crs = dc(pc); g.ccs = dc(1);
+                    g.M = ncol; g.N = P; g.K = io.m;
+                    g.guard_reg = R_PI; g.guard_val = 1;
+                    CK(launch_gemm(g, cwid, pc, mc, w.R, s));
+                    GemmDesc h{};                                       // Y' += T_c Z1
+                    h.A = mat(io.T + c0, io.n, dc(1));
+                    h.B = mat(w.G32, dc(pc), dc(1));
+                    h.C = w.Q; h.crs = dc(pc); h.ccs = dc(1);
+                    h.M = io.m; h.N = P; h.K = ncol;
+                    h.mode = OUT_ACCUM;
+                    h.guard_reg = R_PI; h.guard_val = 1;
+                    CK(launch_gemm(h, mc, pc, cwid, w.R, s));
+                }
+                if ((st = block_orth(w.Q, io.m, mc, R_PI))) return st;
+                k_copy_guarded<<<grid_for((long long)mc * pc, 256, c->sm_count), 256, 0, s>>>(w.Q, w.Y,
+                                                                                           (long long)mc * pc, w.R,
+                                                                                           R_PI, 1);
+                CKL();
             }
-            if ((st = block_orth(w.G32, io.n, ncap, R_PI))) return st;
-            {   // Y = T Z
-                GemmDesc g{};
-                g.A = mat(io.T, io.n, dc(1));
-                g.B = mat(w.G32, dc(pc), dc(1));
-                g.C = w.Y; g.crs = dc(pc); g.ccs = dc(1);
-                g.M = io.m; g.N = P; g.K = io.n;
-                g.guard_reg = R_PI; g.guard_val = 1;
-                CK(launch_gemm(g, mc, pc, ncap, w.R, s));
-            }
-            if ((st = block_orth(w.Y, io.m, mc, R_PI))) return st;
-        } else {
-            // T too wide for the intermediate: Y' = T (T^dagger Q) accumulated over column chunks of T
-            CK(cudaMemsetAsync(w.Q, 0, (size_t)mc * pc * sizeof(float2), s));
-            for (long long c0 = 0; c0 < io.n_cap; c0 += cw) {
-                const int cwid = (int)std::min<long long>(cw, io.n_cap - c0);
-                const Dim ncol = one_chunk ? io.n : dc(cwid);
-                GemmDesc g{};                                       // Z1 = T_c^dagger Q  (cw x p) in the B buffer
-                g.A = mat(io.T + c0, dc(1), io.n, 1);
-                g.B = mat(w.Y, dc(pc), dc(1));
-                g.C = w.G32; g.crs = dc(pc); g.ccs = dc(1);
-                g.M = ncol; g.N = P; g.K = io.m;
-                g.guard_reg = R_PI; g.guard_val = 1;
-                CK(launch_gemm(g, cwid, pc, mc, w.R, s));
-                GemmDesc h{};                                       // Y' += T_c Z1
-                h.A = mat(io.T + c0, io.n, dc(1));
-                h.B = mat(w.G32, dc(pc), dc(1));
-                h.C = w.Q; h.crs = dc(pc); h.ccs = dc(1);
-                h.M = io.m; h.N = P; h.K = ncol;
-                h.mode = OUT_ACCUM;
-                h.guard_reg = R_PI; h.guard_val = 1;
-                CK(launch_gemm(h, mc, pc, cwid, w.R, s));
-            }
-            if ((st = block_orth(w.Q, io.m, mc, R_PI))) return st;
-            k_copy_guarded<<<grid_for((long long)mc * pc, 256, c->sm_count), 256, 0, s>>>(w.Q, w.Y,
-                                                                                       (long long)mc * pc, w.R,
-                                                                                       R_PI, 1);
-            CKL();
         }
         float2* Qb = w.Y;          // orthonormal basis of the sketch
         float2* UB = w.Q;          // eigenvectors of the Gram of B (p x p, column-major)
@@ -483,7 +474,7 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
 }
 
 // ------------------------------------------------------------------ one zip-up sweep
-static qtn_status zip_pass(Ctx* c, Ws& w, qtn_mps* psi, const qtn_mpo* W, int axis, int moff, int mn, int mirror,
+qtn_status zip_pass(Ctx* c, Ws& w, qtn_mps* psi, const qtn_mpo* W, int axis, int moff, int mn, int mirror,
                            const qtn_trunc& tr) {
     cudaStream_t s = c->stream;
     const int N = psi->n_sites, d = psi->d, cap = psi->chi_cap;
@@ -508,7 +499,9 @@ static qtn_status zip_pass(Ctx* c, Ws& w, qtn_mps* psi, const qtn_mpo* W, int ax
             g.C = w.P; g.crs = dr(R_DN); g.ccs = dc(1);
             g.M = dr(R_MID); g.N = dr(R_DN); g.K = dr(R_CHIL);
             g.mode = OUT_STORE; g.alpha_re = 1.f; g.omega_seed = -1;
-            CK(launch_gemm(g, cap * wmax, d * cap, cap, w.R, s));
+            // the site contraction: split-BF16 tensor cores with FP32 accumulation in mixed precision
+            if (tr.prec == QTN_MIXED) CK(launch_gemm_tc(g, cap * wmax, d * cap, cap, w.R, s));
+            else CK(launch_gemm(g, cap * wmax, d * cap, cap, w.R, s));
         }
         const float2* Wc = nullptr;
         const int qm = q - moff;
@@ -542,6 +535,7 @@ static qtn_status zip_pass(Ctx* c, Ws& w, qtn_mps* psi, const qtn_mpo* W, int ax
 
 // Status of a set of flag bits, most severe first.
 static qtn_status flags_status(int f) {
+    if (f & F_TIMEOUT) return QTN_ERR_TIMEOUT;
     if (f & F_NONFINITE) return QTN_ERR_NONFINITE;
     if (f & F_CAPACITY) return QTN_ERR_CAPACITY;
     if (f & F_NOCONV) return QTN_ERR_NOCONV;
@@ -551,7 +545,7 @@ static qtn_status flags_status(int f) {
 // With a statistics struct the call waits for its work, copies the statistics and returns the status of the
 // flags its kernels raised (the flags stay in the sticky status word too, until qtn_check reads them).
 // Without one the call returns at once; its flags are read by the next qtn_check.
-static qtn_status fill_stats(Ctx* c, Ws& w, qtn_stats* st) {
+qtn_status fill_stats(Ctx* c, Ws& w, qtn_stats* st) {
     if (!st) return QTN_OK;
     double hd[L_COUNT];
     int hi[4];
@@ -593,13 +587,7 @@ using namespace qtn;
 
 // ============================================================================ C ABI
 
-struct qtn_context {
-    Ctx c;
-    WsLayout L;        // layout of the workspace the caller sized with qtn_workspace_size
-    int have_layout;
-};
-
-static qtn_status bind_ws(qtn_context* x, void* ws, size_t bytes, Ws& w) {
+qtn_status bind_ws(qtn_context* x, void* ws, size_t bytes, Ws& w) {
     if (!x->have_layout) return QTN_ERR_WORKSPACE;
     qtn_status st = check_ws(x->L, ws, bytes);
     if (st) return st;
@@ -622,7 +610,7 @@ qtn_status qtn_profile(void* ctx, int enable, void* ws, size_t ws_bytes) {
         qtn_status st = bind_ws(x, ws, ws_bytes, w);
         if (st) return st;
         ledger = w.ledger;
-        CK(cudaMemsetAsync(ledger + L_PROF_GEMM, 0, 2 * sizeof(double), x->c.stream));
+        CK(cudaMemsetAsync(ledger + L_PROF_GEMM, 0, 3 * sizeof(double), x->c.stream));
     }
     prof_begin(enable != 0, ledger);
     return QTN_OK;
@@ -630,15 +618,16 @@ qtn_status qtn_profile(void* ctx, int enable, void* ws, size_t ws_bytes) {
 
 qtn_status qtn_profile_read(void* ctx, int kernel_class, double* ms, long long* launches, double* flops, void* ws,
                             size_t ws_bytes) {
-    if (!ctx || !ms || !launches || !flops || kernel_class < 0 || kernel_class > 1) return QTN_ERR_ARG;
+    if (!ctx || !ms || !launches || !flops || kernel_class < 0 || kernel_class > 2) return QTN_ERR_ARG;
     qtn_context* x = (qtn_context*)ctx;
     Ws w;
     qtn_status st = bind_ws(x, ws, ws_bytes, w);
     if (st) return st;
     CK(cudaStreamSynchronize(x->c.stream));
-    prof_read(kernel_class, ms, launches);
-    CK(cudaMemcpy(flops, w.ledger + (kernel_class == 0 ? L_PROF_GEMM : L_PROF_EIG), sizeof(double),
-                  cudaMemcpyDeviceToHost));
+    const int cls = kernel_class == 0 ? PROF_GEMM : (kernel_class == 1 ? PROF_EIG : PROF_TC);
+    const int slot = kernel_class == 0 ? L_PROF_GEMM : (kernel_class == 1 ? L_PROF_EIG : L_PROF_TC);
+    prof_read(cls, ms, launches);
+    CK(cudaMemcpy(flops, w.ledger + slot, sizeof(double), cudaMemcpyDeviceToHost));
     return QTN_OK;
 }
 
@@ -776,9 +765,11 @@ qtn_status qtn_encode(void* ctx, const void* dense, int n, qtn_layout layout, qt
     return fill_stats(c, w, stats);
 }
 
+}  // extern "C"
+
 // Internal: zip-up application without resetting the statistics.
-static qtn_status apply_inner(qtn_context* x, Ws& w, const qtn_mpo* W, int axis, qtn_mps* psi, const qtn_trunc& tr,
-                              bool diag = false) {
+qtn_status apply_inner(qtn_context* x, Ws& w, const qtn_mpo* W, int axis, qtn_mps* psi, const qtn_trunc& tr,
+                       bool diag) {
     const int d = psi->d, N = psi->n_sites;
     int moff = 0, mn = N;
     if (W) {
@@ -808,6 +799,8 @@ static qtn_status apply_inner(qtn_context* x, Ws& w, const qtn_mpo* W, int axis,
     return zip_pass(&x->c, w, psi, W, axis, moff, mn, mirror, tr);
 }
 
+extern "C" {
+
 qtn_status qtn_apply_mpo(void* ctx, const qtn_mpo* W, int axis, qtn_mps* psi, qtn_trunc trunc, qtn_stats* stats,
                          void* ws, size_t ws_bytes) {
     if (!ctx || !W || !psi || !trunc_ok(trunc)) return QTN_ERR_ARG;
@@ -817,7 +810,7 @@ qtn_status qtn_apply_mpo(void* ctx, const qtn_mpo* W, int axis, qtn_mps* psi, qt
     if (st) return st;
     k_reset_stats<<<1, 1, 0, x->c.stream>>>(w.R, w.ledger);
     CKL();
-    st = apply_inner(x, w, W, axis, psi, trunc);
+    st = apply_inner(x, w, W, axis, psi, trunc, false);
     if (st) return st;
     return fill_stats(&x->c, w, stats);
 }
@@ -859,79 +852,74 @@ qtn_status qtn_fresnel_step(void* ctx, qtn_mps* psi, qtn_layout layout, const qt
     for (int step = 0; step < n_steps; ++step)
         for (int o = 0; o < 3; ++o)
             for (int ax = 0; ax < naxes; ++ax) {
-                st = apply_inner(x, w, ops[o], ax, psi, trunc);
+                st = apply_inner(x, w, ops[o], ax, psi, trunc, false);
                 if (st) return st;
             }
     return fill_stats(&x->c, w, stats);
 }
 
+// Runs one FP64 build into `out` and returns its status; synchronises (the host needs w_max).
+static qtn_status run_build64(qtn_context* x, Ws& w, void* ws, int kind, int n, double param, double cutoff,
+                              double gate_cut, int pmax, int flags, qtn_mpo* out) {
+    cudaStream_t s = x->c.stream;
+    if (n > w.L.n_sites) return QTN_ERR_WORKSPACE;
+    char* scratch = (char*)ws + w.L.b64;
+    int* status = w.R + R_TMP3;
+    CK(cudaMemsetAsync(status, 0, sizeof(int), s));
+    CK(launch_build64(kind, n, param, cutoff, gate_cut, pmax, flags, scratch, build64_scratch_bytes(n),
+                      (double*)w.X0, (float2*)out->sites, out->w_cap, out->bond, status, s));
+    std::vector<int> hb(n + 2);
+    CK(cudaMemcpyAsync(hb.data(), out->bond, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hb.data() + n + 1, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hb[n + 1] != QTN_OK) return (qtn_status)hb[n + 1];
+    out->w_max = *std::max_element(hb.begin(), hb.begin() + n + 1);
+    return QTN_OK;
+}
+
 qtn_status qtn_build_qft_mpo(void* ctx, int n, int inverse, double cutoff, qtn_mpo* out, void* ws, size_t ws_bytes) {
-    if (!ctx || !out || n < 1 || out->n_sites != n || out->w_cap < 2) return QTN_ERR_ARG;
+    if (!ctx || !out || n < 1 || n > 62 || out->n_sites != n || out->w_cap < 2 || !(cutoff >= 0.0))
+        return QTN_ERR_ARG;
     qtn_context* x = (qtn_context*)ctx;
     Ws w;
     qtn_status st = bind_ws(x, ws, ws_bytes, w);
     if (st) return st;
-    cudaStream_t s = x->c.stream;
-    const int cap = out->w_cap;
-    if (4 * cap > w.L.m_cap || 2 * cap > w.L.n_cap || w.L.w < 2) return QTN_ERR_WORKSPACE;
-    float2* mt = ws_mtmp(ws, w.L);
-    if ((size_t)n * cap * 4 * cap > (size_t)w.L.n_sites * w.L.chi * w.L.d * w.L.chi || n + 1 > 900)
-        return QTN_ERR_WORKSPACE;
-    int* tb = ws_tmpbond(w);
-    float2* layer = mt + (size_t)n * cap * 4 * cap;
-    int* laybond = tb + 64;
-    qtn_mps stt{n, 4, cap, QTN_CANON_LEFT, inverse ? tb : out->bond, inverse ? (void*)mt : out->sites};
-    k_reset_stats<<<1, 1, 0, s>>>(w.R, w.ledger);
-    CKL();
-    k_identity_mpo_state<<<n, 32, 0, s>>>((float2*)stt.sites, stt.bond, n, cap);
-    CKL();
-    qtn_trunc tr{cap, cutoff, QTN_PLAIN_FP32, 0};
-    for (int j = 0; j < n; ++j) {
-        k_qft_layer<<<n, 32, 0, s>>>(layer, laybond, n, j, 2);
-        CKL();
-        qtn_mpo L{n, 2, 2, laybond, layer};
-        const int mirror = (stt.canon == QTN_CANON_LEFT) ? 1 : 0;
-        st = zip_pass(&x->c, w, &stt, &L, 0, 0, n, mirror, tr);
-        if (st) return st;
-    }
-    if (inverse) {
-        k_mpo_dagger<<<n, 128, 0, s>>>(mt, tb, cap, (float2*)out->sites, out->bond, cap, n);
-        CKL();
-    }
-    std::vector<int> hb(n + 1);
-    CK(cudaMemcpyAsync(hb.data(), out->bond, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    out->w_max = *std::max_element(hb.begin(), hb.end());
-    return QTN_OK;
+    return run_build64(x, w, ws, BUILD64_QFT, n, 0.0, cutoff, 0.0, 0, inverse ? 1 : 0, out);
 }
 
 qtn_status qtn_build_phase_mpo(void* ctx, int n, double c, int bit_reversed, double cutoff, qtn_mpo* out, void* ws,
                                size_t ws_bytes) {
-    if (!ctx || !out || n < 1 || n > 24 || out->n_sites != n || out->w_cap < 1) return QTN_ERR_ARG;
+    if (!ctx || !out || n < 1 || n > 62 || out->n_sites != n || out->w_cap < 1 || !isfinite(c) || !(cutoff >= 0.0))
+        return QTN_ERR_ARG;
     qtn_context* x = (qtn_context*)ctx;
     Ws w;
     qtn_status st = bind_ws(x, ws, ws_bytes, w);
     if (st) return st;
-    cudaStream_t s = x->c.stream;
-    const int cap = out->w_cap;
-    if ((1ll << n) > w.L.dense || 2 * cap > w.L.m_cap) return QTN_ERR_WORKSPACE;
-    // the temporary d = 2 MPS lives in the MPS-sized scratch (n_sites x chi x d x chi of the sizing call)
-    if ((size_t)n * cap * 2 * cap > (size_t)w.L.n_sites * w.L.chi * w.L.d * w.L.chi) return QTN_ERR_WORKSPACE;
-    float2* mt = ws_mtmp(ws, w.L);
-    int* tb = ws_tmpbond(w);
-    k_phase_vector<<<grid_for(1ll << n, 256, x->c.sm_count), 256, 0, s>>>(w.X1, n, c, bit_reversed);
-    CKL();
-    qtn_mps tmp{n, 2, cap, QTN_CANON_NONE, tb, mt};
-    qtn_trunc tr{cap, cutoff, QTN_PLAIN_FP32, 0};
-    st = qtn_encode(ctx, w.X1, n, QTN_LAYOUT_1D, tr, &tmp, nullptr, ws, ws_bytes);
+    return run_build64(x, w, ws, BUILD64_QPHASE, n, c, cutoff, 0.0, 0, bit_reversed ? 0 : 2, out);
+}
+
+qtn_status qtn_build_bessel_mpo(void* ctx, int n, double t, int p_max, int bit_reversed, qtn_mpo* out, void* ws,
+                                size_t ws_bytes) {
+    if (!ctx || !out || n < 1 || n > 62 || out->n_sites != n || p_max < 0 || !isfinite(t)) return QTN_ERR_ARG;
+    if (2 * p_max + 1 > BUILD64_BOND_CAP || 2 * p_max + 1 > out->w_cap) return QTN_ERR_CAPACITY;
+    qtn_context* x = (qtn_context*)ctx;
+    Ws w;
+    qtn_status st = bind_ws(x, ws, ws_bytes, w);
     if (st) return st;
-    k_diag_mpo<<<n, 128, 0, s>>>(mt, cap, tb, (float2*)out->sites, cap, out->bond, n);
-    CKL();
-    std::vector<int> hb(n + 1);
-    CK(cudaMemcpyAsync(hb.data(), out->bond, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    out->w_max = *std::max_element(hb.begin(), hb.end());
-    return QTN_OK;
+    return run_build64(x, w, ws, BUILD64_BESSEL, n, t, 0.0, 0.0, p_max, bit_reversed ? 0 : 2, out);
+}
+
+qtn_status qtn_build_pauliz_mpo(void* ctx, int n, double t, double gate_cutoff, int bit_reversed, double cutoff,
+                                qtn_mpo* out, void* ws, size_t ws_bytes) {
+    if (!ctx || !out || n < 1 || n > 24 || out->n_sites != n || out->w_cap < 1 || !isfinite(t) ||
+        !(gate_cutoff >= 0.0) || !(cutoff >= 0.0))
+        return QTN_ERR_ARG;
+    qtn_context* x = (qtn_context*)ctx;
+    Ws w;
+    qtn_status st = bind_ws(x, ws, ws_bytes, w);
+    if (st) return st;
+    if ((1ll << n) > w.L.dense) return QTN_ERR_WORKSPACE;   // the 2^n Walsh-Hadamard coefficients
+    return run_build64(x, w, ws, BUILD64_PAULIZ, n, t, cutoff, gate_cutoff, 0, bit_reversed ? 0 : 2, out);
 }
 
 __global__ void k_copy_cols(const float2* __restrict__ U, int ldu, const int* __restrict__ perm, float2* __restrict__ out,
@@ -1292,7 +1280,7 @@ qtn_status qtn_batch_create(int count, void* const* ctxs, qtn_mps* items, const 
         count_launch(PROF_OTHER, 0, false);
         for (int step = 0; step < n_steps && st == QTN_OK; ++step)
             for (int o = 0; o < 3 && st == QTN_OK; ++o)
-                for (int ax = 0; ax < naxes && st == QTN_OK; ++ax) st = apply_inner(x, w, ops[o], ax, psi, trunc);
+                for (int ax = 0; ax < naxes && st == QTN_OK; ++ax) st = apply_inner(x, w, ops[o], ax, psi, trunc, false);
         cudaGraph_t g = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(s, &g);
         // capturing executed nothing: the item is unchanged, so is its canonical form
@@ -1403,7 +1391,7 @@ constexpr WsLayout noalloc_layout() {
     L.Z = take(std::max(gdim * nc, pc * pc) * c8);
     L.total = off;
     // regions of the zip-up and of the dense transforms: not used by the truncated SVD (bound to null)
-    L.T = L.P = L.carry = L.S64 = L.omega = L.X0 = L.X1 = WS_UNUSED;
+    L.T = L.P = L.carry = L.S64 = L.omega = L.X0 = L.X1 = L.b64 = WS_UNUSED;
     return L;
 }
 constexpr WsLayout kNoallocLayout = noalloc_layout();

@@ -11,6 +11,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 
 #include "../../include/qtn.h"
 
@@ -120,7 +121,7 @@ struct GemmDesc {
 
 // ------------------------------------------------------------------ ledger (device doubles in the workspace)
 // Flag bits of R_FLAGS / R_STICKY.
-enum Flag : int { F_NOCONV = 1, F_CAPACITY = 2, F_NONFINITE = 4 };
+enum Flag : int { F_NOCONV = 1, F_CAPACITY = 2, F_NONFINITE = 4, F_TIMEOUT = 8 };
 __device__ __forceinline__ void raise_flag(int* R, int bit) {
     atomicOr(&R[R_FLAGS], bit);
     atomicOr(&R[R_STICKY], bit);
@@ -135,17 +136,18 @@ enum Ledger : int {
     L_MAXBOND,
     L_PROF_GEMM = 8,  // profiling: algorithmic FLOPs of GEMM launches (8 M N K per complex GEMM)
     L_PROF_EIG = 9,   // profiling: algorithmic FLOPs of the shared-memory eigensolver
+    L_PROF_TC = 10,   // profiling: algorithmic FLOPs of the tensor-core site contraction (8 M N K)
     L_COUNT = 16
 };
 
 // ------------------------------------------------------------------ launch accounting and profiling
-enum ProfClass : int { PROF_GEMM = 0, PROF_EIG = 1, PROF_OTHER = 2, PROF_NCLASS = 3 };
+enum ProfClass : int { PROF_GEMM = 0, PROF_EIG = 1, PROF_OTHER = 2, PROF_TC = 3, PROF_NCLASS = 4 };
 void count_launch(int cls, cudaStream_t s, bool before);   // brackets a launch with events when profiling
 extern double* g_prof_ledger;                              // ledger receiving device FLOP counts (or null)
 
 // ------------------------------------------------------------------ workspace layout
 struct WsLayout {
-    size_t ledger, regs, T, P, carry, G64, G32, U, lam, Y, Q, S64, Z, X0, X1, omega, total;
+    size_t ledger, regs, T, P, carry, G64, G32, U, lam, Y, Q, S64, Z, X0, X1, omega, b64, total;
     int m_cap, n_cap, p_cap, chi, d, w, n_sites;
     long long dense;
 };
@@ -181,11 +183,57 @@ constexpr int EIG_MAX = 160;
 // memory (cudaFuncSetAttribute acts on the current device only); thread-safe, once per device.
 cudaError_t configure_device_kernels(int device);
 
+// FP64 operator builders (k_build64.cu): kinds, scratch size, launch.
+enum Build64Op : int { BUILD64_QFT = 0, BUILD64_QPHASE = 1, BUILD64_PAULIZ = 2, BUILD64_BESSEL = 3 };
+constexpr int BUILD64_BOND_CAP = 32;   // largest bond of an operator built in FP64
+size_t build64_scratch_bytes(int n);
+cudaError_t launch_build64(int kind, int n, double param, double cutoff, double gate_cut, int pmax, int flags,
+                           void* scratch, size_t scratch_bytes, double* wh, float2* out, int ocap, int* obond,
+                           int* status, cudaStream_t s);
+
 // ------------------------------------------------------------------ launches (defined in the .cu files)
 cudaError_t launch_gemm(const GemmDesc& d, int max_m, int max_n, int max_k, const int* R, cudaStream_t s);
+// Split-BF16 tensor-core complex GEMM (STORE/ACCUM only), FP32 accumulation in TMEM (k_tc.cu).
+cudaError_t launch_gemm_tc(const GemmDesc& d, int max_m, int max_n, int max_k, const int* R, cudaStream_t s);
 cudaError_t launch_refine_basis(const double2* G, Dim ld, Dim r, float2* V, int ldv, const int* R, cudaStream_t s);
 cudaError_t launch_eig(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, double* lam, const int* R,
                        int r_cap, int max_sweeps, double* ledger, cudaStream_t s, int guard_reg = -1, int guard_val = 0,
                        float tol = 1e-6f, float dead_rel = 0.f, bool report_nonconv = true);
 
 }  // namespace qtn
+
+// ------------------------------------------------------------------ host-side helpers shared by the entry points
+#define CK(expr)                                                                                          \
+    do {                                                                                                  \
+        cudaError_t _e = (expr);                                                                          \
+        if (_e != cudaSuccess) {                                                                          \
+            fprintf(stderr, "qtn: CUDA error %s at %s:%d\n", cudaGetErrorString(_e), __FILE__, __LINE__); \
+            return QTN_ERR_CUDA;                                                                          \
+        }                                                                                                 \
+    } while (0)
+#define CKL()                                         \
+    do {                                              \
+        qtn::count_launch(qtn::PROF_OTHER, 0, false); \
+        CK(cudaGetLastError());                       \
+    } while (0)
+
+namespace qtn {
+bool trunc_ok(const qtn_trunc& t);
+int grid_for(long long n, int threads, int sm);
+qtn_status fill_stats(Ctx* c, Ws& w, qtn_stats* st);
+qtn_status zip_pass(Ctx* c, Ws& w, qtn_mps* psi, const qtn_mpo* W, int axis, int moff, int mn, int mirror,
+                    const qtn_trunc& tr);
+__global__ void k_reset_stats(int* R, double* ledger);
+}  // namespace qtn
+
+// Library context bound to a stream, with the layout of the workspace the caller sized.
+struct qtn_context {
+    qtn::Ctx c;
+    qtn::WsLayout L;
+    int have_layout;
+};
+qtn_status bind_ws(qtn_context* x, void* ws, size_t bytes, qtn::Ws& w);
+// One zip-up application of W on `axis` (diag: W is an MPS seen as a diagonal operator, axis 2/3), bringing
+// psi to a canonical form first when it has none.
+qtn_status apply_inner(qtn_context* x, qtn::Ws& w, const qtn_mpo* W, int axis, qtn_mps* psi, const qtn_trunc& tr,
+                       bool diag);

@@ -36,7 +36,8 @@ EXPORTS = (
     "qtn_kron_interleave", "qtn_add", "qtn_launch_count", "qtn_profile", "qtn_profile_read", "qtn_tsvd_noalloc",
     "qtn_hadamard", "qtn_scale", "qtn_hadamard_zipup", "qtn_overlap_grad",
     "qtn_batch_create", "qtn_batch_launch", "qtn_batch_destroy", "qtn_batch_sync",
-    "qtn_workspace_init", "qtn_check",
+    "qtn_workspace_init", "qtn_check", "qtn_build_bessel_mpo", "qtn_build_pauliz_mpo",
+    "qtn_reverse_sites", "qtn_psf", "qtn_convolve", "qtn_astf_field", "qtn_transfer_step", "qtn_project_apply",
 )
 
 
@@ -86,6 +87,8 @@ def load_library(path: str = LIB_PATH):
         "qtn_encode": [P, P, I, I, tr, mp, st, P, S],
         "qtn_build_qft_mpo": [P, I, I, D, op, P, S],
         "qtn_build_phase_mpo": [P, I, D, I, D, op, P, S],
+        "qtn_build_bessel_mpo": [P, I, D, I, I, op, P, S],
+        "qtn_build_pauliz_mpo": [P, I, D, D, I, D, op, P, S],
         "qtn_mpo_dagger": [P, op, op],
         "qtn_apply_mpo": [P, op, I, mp, tr, st, P, S],
         "qtn_truncate": [P, mp, tr, st, P, S],
@@ -106,6 +109,12 @@ def load_library(path: str = LIB_PATH):
                              ctypes.POINTER(P)],
         "qtn_batch_launch": [P, I],
         "qtn_batch_sync": [P],
+        "qtn_reverse_sites": [P, mp],
+        "qtn_project_apply": [P, op, I, mp, mp, P, S],
+        "qtn_psf": [P, mp, op, I, tr, mp, st, P, S],
+        "qtn_convolve": [P, mp, mp, op, op, tr, st, P, S],
+        "qtn_astf_field": [P, I, D, D, I, P, LL],
+        "qtn_transfer_step": [P, mp, op, op, mp, tr, st, P, S],
         "qtn_workspace_init": [P, P, S],
         "qtn_check": [P, P, S],
         "qtn_batch_destroy": [P],
@@ -296,6 +305,19 @@ class Engine:
                                             *self._ws()), "qtn_build_phase_mpo")
         return m
 
+    def build_bessel_mpo(self, n: int, t: float, p_max: int, w_cap: int = 32, bit_reversed: bool = True) -> MPO:
+        m = MPO(n, w_cap)
+        _check(self.lib.qtn_build_bessel_mpo(self.ctx, n, float(t), int(p_max), int(bit_reversed), ctypes.byref(m.c),
+                                             *self._ws()), "qtn_build_bessel_mpo")
+        return m
+
+    def build_pauliz_mpo(self, n: int, t: float, gate_cutoff: float, cutoff: float = 1e-12, w_cap: int = 32,
+                         bit_reversed: bool = True) -> MPO:
+        m = MPO(n, w_cap)
+        _check(self.lib.qtn_build_pauliz_mpo(self.ctx, n, float(t), float(gate_cutoff), int(bit_reversed),
+                                             float(cutoff), ctypes.byref(m.c), *self._ws()), "qtn_build_pauliz_mpo")
+        return m
+
     def mpo_dagger(self, W: MPO) -> MPO:
         out = MPO(W.n_sites, W.c.w_cap)
         _check(self.lib.qtn_mpo_dagger(self.ctx, ctypes.byref(W.c), ctypes.byref(out.c)), "qtn_mpo_dagger")
@@ -389,6 +411,48 @@ class Engine:
     def add(self, a: MPS, b: MPS, out: MPS) -> MPS:
         _check(self.lib.qtn_add(self.ctx, ctypes.byref(a.c), ctypes.byref(b.c), ctypes.byref(out.c)), "qtn_add")
         return out
+
+    def project_apply(self, W, axis: int, ket: MPS, frame: MPS) -> MPS:
+        """frame <- V V^dagger W ket: the frame's centre replaced (qtn_project_apply; W None = identity)."""
+        _check(self.lib.qtn_project_apply(self.ctx, ctypes.byref(W.c) if W is not None else None, int(axis),
+                                          ctypes.byref(ket.c), ctypes.byref(frame.c), *self._ws()),
+               "qtn_project_apply")
+        return frame
+
+    def reverse_sites(self, psi: MPS) -> MPS:
+        _check(self.lib.qtn_reverse_sites(self.ctx, ctypes.byref(psi.c)), "qtn_reverse_sites")
+        return psi
+
+    def psf(self, phi: MPS, Q: MPO, psf: MPS, chi_max: int, cutoff: float, centre: bool = False,
+            stats: bool = True):
+        """phi <- normalised U_qft phi (natural frequency order); psf <- |phi|^2 as an MPS (qtn_psf)."""
+        st = c_stats()
+        _check(self.lib.qtn_psf(self.ctx, ctypes.byref(phi.c), ctypes.byref(Q.c), int(centre),
+                                self.trunc(chi_max, cutoff), ctypes.byref(psf.c), ctypes.byref(st) if stats else None,
+                                *self._ws()), "qtn_psf")
+        return _stats(st) if stats else None
+
+    def convolve(self, a: MPS, b: MPS, Q: MPO, Qd: MPO, chi_max: int, cutoff: float, stats: bool = True):
+        """b <- a (*) b (circular convolution); a is overwritten by its transform (qtn_convolve)."""
+        st = c_stats()
+        _check(self.lib.qtn_convolve(self.ctx, ctypes.byref(a.c), ctypes.byref(b.c), ctypes.byref(Q.c),
+                                     ctypes.byref(Qd.c), self.trunc(chi_max, cutoff),
+                                     ctypes.byref(st) if stats else None, *self._ws()), "qtn_convolve")
+        return _stats(st) if stats else None
+
+    def astf_field(self, n: int, z_over_lambda: float, lambda_over_dx: float, bit_reversed: bool = True):
+        L = 1 << n
+        out = torch.empty((L, L), dtype=torch.complex64, device="cuda")
+        _check(self.lib.qtn_astf_field(self.ctx, n, float(z_over_lambda), float(lambda_over_dx), int(bit_reversed),
+                                       ctypes.c_void_p(out.data_ptr()), out.numel()), "qtn_astf_field")
+        return out
+
+    def transfer_step(self, psi: MPS, Q: MPO, Qd: MPO, T: MPS, chi_max: int, cutoff: float, stats: bool = True):
+        st = c_stats()
+        _check(self.lib.qtn_transfer_step(self.ctx, ctypes.byref(psi.c), ctypes.byref(Q.c), ctypes.byref(Qd.c),
+                                          ctypes.byref(T.c), self.trunc(chi_max, cutoff),
+                                          ctypes.byref(st) if stats else None, *self._ws()), "qtn_transfer_step")
+        return _stats(st) if stats else None
 
     def check(self):
         """Raises QtnError for any device-side failure since the last check (qtn_check)."""

@@ -192,3 +192,16 @@ def random_unitary_sites(n: int, seed: int, dim: int = 2):
         q = q * (np.diag(r) / np.abs(np.diag(r)))[None, :]
         out.append(q)
     return out
+
+
+def pupil_field(n: int, alpha: float = 0.001, r0: float = 0.5, dtype=np.complex64) -> np.ndarray:
+    """Aberrated pupil E_0 = A(r) exp(-i Phi(u, v)) on (u, v) in [-1, 1)^2 (Sec. V, Eq. field): a soft-edged
+    disk A(r) = 1 / (1 + exp((r - r0) / alpha)) and the paper's test phase
+    Phi(u, v) = cos(u) cos(u) + cos(2u + 5v) + sin(u v) + cos(2u + 2v)^13.  Row index = u, column index = v."""
+    L = 1 << n
+    t = (np.arange(L) + 0.5) / L * 2.0 - 1.0
+    u, v = np.meshgrid(t, t, indexing="ij")
+    r = np.sqrt(u * u + v * v)
+    A = 0.5 * (1.0 - np.tanh((r - r0) / (2.0 * alpha)))    # = 1 / (1 + exp((r - r0)/alpha)), overflow-free
+    phi = np.cos(u) * np.cos(u) + np.cos(2 * u + 5 * v) + np.sin(u * v) + np.cos(2 * u + 2 * v) ** 13
+    return (A * np.exp(-1j * phi)).astype(dtype)

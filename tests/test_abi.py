@@ -61,9 +61,8 @@ def test_no_cpu_fallback_in_the_product_path():
             assert "import oracle" not in src and "from oracle" not in src, f
 
 
-def test_mixed_precision_rejected_without_gpu(libpath):
-    # QTN_MIXED is reserved (the BF16 tensor-core path is not built): the truncation rule is checked
-    # before any pointer is used or any CUDA call is made
+def test_bad_truncation_rule_rejected_without_gpu(libpath):
+    # an unknown precision or a negative cutoff is rejected before any pointer is used or any CUDA call is made
     class Trunc(ctypes.Structure):
         _fields_ = [("chi_max", ctypes.c_int), ("cutoff", ctypes.c_double), ("prec", ctypes.c_int),
                     ("max_sweeps", ctypes.c_int)]
@@ -72,13 +71,13 @@ def test_mixed_precision_rejected_without_gpu(libpath):
     k = ctypes.c_int(0)
     args = (buf, 2, 2)
     tail = (buf, buf, 2, ctypes.byref(k), None, None)
-    assert lib.qtn_tsvd_noalloc(*args, Trunc(2, 1e-10, 1, 0), *tail) == 1
+    assert lib.qtn_tsvd_noalloc(*args, Trunc(2, 1e-10, 7, 0), *tail) == 1       # neither FP32 nor mixed
     assert lib.qtn_tsvd_noalloc(*args, Trunc(2, -1.0, 0, 0), *tail) == 1      # negative cutoff
 
 
-def test_bench_refuses_mixed_precision():
+def test_bench_rejects_an_unknown_precision():
     import subprocess
     import sys
-    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--prec", "mixed"], capture_output=True,
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--prec", "fp8"], capture_output=True,
                        text=True, timeout=300)
-    assert r.returncode == 2 and "not built" in r.stderr
+    assert r.returncode == 2 and "invalid choice" in r.stderr

@@ -139,13 +139,3 @@ def test_tsvd_tall_rank_deficient(lib, eng_big, m, n, rank):
     T64 = T.astype(np.complex128)
     assert np.linalg.norm(U @ C - T64) / np.linalg.norm(T64) < 2e-6
     assert U.shape[1] <= rank + 2
-
-
-def test_mixed_precision_is_rejected(lib):
-    """QTN_MIXED is reserved (BF16 tensor-core contractions are not built): calls taking it return QTN_ERR_ARG."""
-    eng = lib.Engine(n_sites=4, d=4, chi=8, w=4, dense=1 << 8)
-    psi = lib.MPS.from_numpy_sites(synth.random_mps_sites([1, 2, 4, 2, 1], 4, seed=77), 8)
-    with pytest.raises(lib.QtnError) as err:
-        eng.truncate(psi, 8, 1e-10, prec="mixed")
-    assert err.value.code == 1          # QTN_ERR_ARG
-    eng.truncate(psi, 8, 1e-10)          # the plain path still runs

@@ -91,3 +91,10 @@ def test_batch_rejects_an_item_in_no_canonical_form(eng, lib):
     with pytest.raises(lib.QtnError) as ei:
         lib.Batch([e2], [psi], [Q], [Qd], [D], n_steps=1, chi_max=16, cutoff=1e-10)
     assert ei.value.code == 1                                       # QTN_ERR_ARG
+
+
+def test_unknown_precision_is_rejected(eng, lib):
+    psi = lib.MPS.from_numpy_sites(synth.random_mps_sites([1, 2, 4, 2, 1], 4, seed=77), 8)
+    tr = lib.c_trunc(8, 1e-10, 7, 0)                                 # neither QTN_PLAIN_FP32 nor QTN_MIXED
+    code = eng.lib.qtn_truncate(eng.ctx, ctypes.byref(psi.c), tr, None, *eng._ws())
+    assert code == 1                                                 # QTN_ERR_ARG

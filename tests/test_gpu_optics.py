@@ -137,3 +137,80 @@ def test_site_gradient_matches_oracle_finite_differences(lib, eng):
                 assert abs(fd - pred) <= 1e-3 * np.abs(grad).max() + 1e-3 * abs(fd), (p, k, s, m, unit)
                 checked += 1
     assert checked == 16 and bonds[0] == 1
+
+
+# ----------------------------------------------------------------------------- adjoints at a truncated size
+
+def truncated_case(lib, eng, chi):
+    """n = 6 problem whose passes truncate (chi below the full bond 64); inputs built by the oracle side and
+    uploaded, so both sides start from the same field, mask and target."""
+    from paper_2510_23089_gb300 import optics
+    from oracle import mpo as OM
+    n, c = 6, 0.5
+    E = synth.gaussian_beam_with_rectangles(n, seed=621, waist=0.2).astype(np.complex128)
+    E_sites, _ = OS.tt_svd(OQ.dense_to_quantics(E, "interleaved"), n, 4, 64, 1e-14)
+    mx, my = synth.smooth_random_phase_mask_factors(n, seed=622, strength=0.5)
+    X, _ = OS.tt_svd(mx, n, 2, 64, 1e-14)
+    Y, _ = OS.tt_svd(my, n, 2, 64, 1e-14)
+    M_sites = OS.kron_interleave(X, Y)
+    It = synth.rectangles_target(n, seed=623).astype(np.float64)
+    Em = lib.MPS.from_numpy_sites(E_sites, 128, "left")
+    M = lib.MPS.from_numpy_sites(M_sites, 64, "none")
+    Itm = lib.MPS(n, 4, 64)
+    eng.encode(torch.from_numpy(It.astype(np.complex64)).cuda(), n, "interleaved", Itm, 64, 1e-14, stats=False)
+    Q = OM.qft_mpo_layers(n, 1e-12)
+    ops = (Q, OM.dagger(Q), OM.phase_mpo(n, c, 1e-12))
+    probs = {a: optics.IntensityLossProblem(eng, n, c, chi=chi, cutoff=1e-12, chi_intensity=128, adjoint=a)
+             for a in ("frozen", "exact")}
+    return probs, Em, M, Itm, E_sites, M_sites, OQ.dense_to_quantics(It, "interleaved"), ops, n
+
+
+def test_frozen_adjoint_matches_oracle_frozen_gradient(lib, eng):
+    from oracle import optics as OO
+    chi = 12
+    probs, Em, M, Itm, E_sites, M_sites, It, ops, n = truncated_case(lib, eng, chi)
+    loss, cache = probs["frozen"].forward(Em, M, Itm)
+    G, H = probs["frozen"].backward(Em, M, cache)
+    L_o, G_o, _ = OO.frozen_loss_and_grad(E_sites, M_sites, It, n, ops, chi, 1e-12)
+    got = eng.to_dense(G, "interleaved", n).cpu().numpy().astype(np.complex128)
+    ref = OQ.quantics_to_dense(G_o, n, "interleaved")
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    print(f"frozen adjoint at chi {chi}: loss rel {abs(loss - L_o) / L_o:.2e}, gradient rel {err:.2e}")
+    assert abs(loss - L_o) <= 1e-3 * L_o
+    assert err <= 1e-3
+
+
+def test_exact_adjoint_against_finite_differences_of_the_truncated_map(lib, eng):
+    # the oracle recomputes every truncation for each perturbed mask: central differences of the truncated
+    # forward map along single site entries, against the site gradient of the "exact" adjoint
+    from oracle import optics as OO
+    chi = 12
+    probs, Em, M, Itm, E_sites, M_sites, It, ops, n = truncated_case(lib, eng, chi)
+    sites = M.sites.clone()
+    x = sites.clone().requires_grad_(True)
+    from paper_2510_23089_gb300 import optics
+    loss = optics.FresnelIntensityLoss.apply(x, probs["exact"], Em, M, Itm)
+    loss.backward()
+    grad = x.grad.cpu().numpy().astype(np.complex128)
+
+    def oracle_loss(ms):
+        L, _, _ = OO.frozen_loss_and_grad(E_sites, ms, It, n, ops, chi, 1e-12)
+        return L
+
+    base = [A.copy() for A in M_sites]
+    rng = np.random.default_rng(11)
+    h = 1e-6
+    errs = []
+    for p in (1, 3, 4):
+        a, d, b = base[p].shape
+        for _ in range(2):
+            k, s, m = rng.integers(a), rng.integers(d), rng.integers(b)
+            sp = [A.copy() for A in base]
+            sm = [A.copy() for A in base]
+            sp[p][k, s, m] += h
+            sm[p][k, s, m] -= h
+            fd = (oracle_loss(sp) - oracle_loss(sm)) / (2 * h)
+            pred = np.real(grad[p, k, s, m])
+            errs.append(abs(fd - pred) / np.abs(grad).max())
+    print(f"exact adjoint vs finite differences of the truncated map (chi {chi}): max rel {max(errs):.2e}")
+    assert max(errs) <= 1e-2

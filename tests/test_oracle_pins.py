@@ -450,3 +450,164 @@ def test_schmidt_spectra_match_dense_unfoldings():
         r = len(s)
         assert np.allclose(s, s_ref[:r], rtol=0, atol=1e-12 * s_ref[0])
         assert np.all(s_ref[r:] < 1e-12 * s_ref[0])
+
+
+# ----------------------------------------------------------------------------- lattice dispersion (Sec. VI.B)
+
+@pytest.mark.parametrize("n", [4, 6, 8])
+@pytest.mark.parametrize("bit_reversed", [True, False])
+def test_bessel_mpo_reaches_1e10_at_pmax_14(n, bit_reversed):
+    # Sec. VI.B.4, Fig. fig_error_mpo: at p_max = 14 (bond 29) the operator error is below 1e-10 for t = 1
+    W = OM.bessel_mpo(n, 1.0, 14, bit_reversed)
+    assert max(OM.bonds(W)) == 29
+    assert np.abs(OM.diag_of(W) - OM.lattice_diagonal(n, 1.0, bit_reversed)).max() < 1e-10
+
+
+@pytest.mark.parametrize("p_max", [2, 4, 6])
+def test_bessel_truncation_within_the_bessel_tail_bound(p_max):
+    # delta(p_max) <= sum_{|p| > p_max} |J_p(t)| since every plane-wave term has unit modulus (Sec. VI.B.4)
+    from scipy.special import jv
+    t, n = 2.0, 6
+    err = np.abs(OM.diag_of(OM.bessel_mpo(n, t, p_max)) - OM.lattice_diagonal(n, t)).max()
+    tail = 2 * sum(abs(jv(p, t)) for p in range(p_max + 1, 60))
+    assert err <= tail * (1 + 1e-9)
+    assert err > 0.1 * tail          # and the bound is not loose by orders of magnitude
+
+
+def test_walsh_coefficients_match_definition_and_product_formula():
+    # Eq. coeff_trace by brute force, and the closed product form Eq. eq_cs:
+    # c_S = 2^-n Re prod_j (1 + (-1)^[j in S] e^{i theta_j}), theta_j = 2 pi / 2^j, qubit j = bit n-j of k
+    n = 5
+    L = 1 << n
+    eps = np.cos(2 * np.pi * np.arange(L) / L)
+    c = OM.walsh_coefficients(eps)
+    for S in range(L):
+        brute = sum(eps[s] * (-1) ** bin(S & s).count("1") for s in range(L)) / L
+        prod = 1.0 + 0j
+        for j in range(1, n + 1):
+            inS = (S >> (n - j)) & 1
+            prod *= 1 + (-1) ** inS * np.exp(2j * np.pi / 2 ** j)
+        assert abs(c[S] - brute) < 1e-14
+        assert abs(c[S] - prod.real / L) < 1e-14
+
+
+@pytest.mark.parametrize("gate_cutoff", [0.0, 1e-6, 1e-3])
+def test_pauliz_circuit_error_within_the_dropped_gate_bound(gate_cutoff):
+    # ||U - U_trunc|| <= t sum_{dropped} |c_S| (Sec. VI.B.3); with every gate kept the circuit is exact
+    n, t = 8, 1.0
+    L = 1 << n
+    c = OM.walsh_coefficients(np.cos(2 * np.pi * np.arange(L) / L))
+    dropped = np.abs(c[1:][np.abs(c[1:]) < gate_cutoff]).sum()
+    W = OM.pauliz_mpo(n, t, gate_cutoff, cutoff=0.0)
+    err = np.abs(OM.diag_of(W) - OM.lattice_diagonal(n, t)).max()
+    assert err <= t * dropped + 1e-12
+    if gate_cutoff == 0.0:
+        assert err < 1e-12
+
+
+def test_lattice_transfer_reduces_to_fresnel_near_zero_frequency():
+    # Sec. VI.B.1: cos k ~ 1 - k^2/2, so exp(-i t cos(2 pi k / L)) ~ exp(-i t) exp(+i t (2 pi k / L)^2 / 2) near k = 0
+    n, t = 8, 3.0
+    L = 1 << n
+    k = np.arange(8)
+    D = OM.lattice_diagonal(n, t, False)[k]
+    approx = np.exp(-1j * t) * np.exp(1j * t * (2 * np.pi * k / L) ** 2 / 2)
+    assert np.abs(D - approx).max() < t * (2 * np.pi * 8 / L) ** 4 / 24 + 1e-12
+
+
+# ----------------------------------------------------------------------------- imaging and angular spectrum
+
+def test_psf_of_a_box_aperture_is_the_dirichlet_kernel():
+    # |sum_{j<w} e^{2 pi i j k / L}|^2 = sin^2(pi w k / L) / sin^2(pi k / L): the PSF of a w x w box pupil factors
+    from oracle import optics as OO
+    n, w = 5, 7
+    L = 1 << n
+    E = np.zeros((L, L), complex)
+    E[:w, :w] = 1.0
+    k = np.arange(L)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        dk = np.where(k == 0, w * w, np.sin(np.pi * w * k / L) ** 2 / np.sin(np.pi * k / L) ** 2)
+    ref = np.outer(dk, dk)
+    ref = ref / ref.sum()
+    assert np.abs(OO.psf_dense(E) - ref).max() < 1e-14
+    c = OO.psf_dense(E, centre=True)
+    assert abs(c.sum() - 1) < 1e-12 and np.argmax(c) == (L // 2) * L + L // 2
+
+
+def test_circular_convolution_matches_fft_witness():
+    # the paper's pin for Eq. convolution_eq: on the finite grid it is the FFT computation (library witness)
+    from oracle import optics as OO
+    rng = np.random.default_rng(5)
+    a = rng.standard_normal((16, 16)) + 1j * rng.standard_normal((16, 16))
+    b = rng.standard_normal((16, 16))
+    ref = np.fft.ifft2(np.fft.fft2(a) * np.fft.fft2(b))
+    assert np.abs(OO.convolve_dense(a, b) - ref).max() < 1e-12
+
+
+def test_astf_reduces_to_fresnel_in_the_paraxial_limit_and_decays_when_evanescent():
+    # Sec. VI.A: sqrt(1 - u) ~ 1 - u/2 gives exp(-i pi lambda z f^2) per axis, the Fresnel transfer function;
+    # the neglected term is (z/lambda) 2 pi u^2 / 8 at most
+    from oracle import optics as OO
+    n = 6
+    L = 1 << n
+    zl, ld = 40.0, 0.0633
+    T = OO.astf_transfer(n, zl, ld)
+    kf = OM.fftfreq_int(L).astype(float)
+    c = zl * ld * ld / L                      # lambda z / (L dx^2)
+    Tf = np.exp(-1j * np.pi * c * kf ** 2 / L)
+    u_max = 2 * (ld / 2) ** 2
+    assert np.abs(T - np.outer(Tf, Tf)).max() <= 2 * np.pi * zl * u_max ** 2 / 8 * 1.01
+    assert np.allclose(np.abs(T), 1.0)
+    Te = OO.astf_transfer(n, 3.0, 1.5)       # lambda = 1.5 dx: the outer frequencies are evanescent
+    lf = 1.5 * kf / L
+    u = lf[:, None] ** 2 + lf[None, :] ** 2
+    assert np.allclose(np.abs(Te[u <= 1]), 1.0)
+    assert np.all(np.abs(Te[u > 1]) < 1.0)
+    assert np.allclose(np.abs(Te[u > 1]), np.exp(-2 * np.pi * 3.0 * np.sqrt(u[u > 1] - 1)))
+
+
+# ----------------------------------------------------------------------------- frozen-projector adjoint
+
+def _frozen_case(n, chi):
+    from oracle import optics as OO
+    E = synth.gaussian_beam_with_rectangles(n, seed=931, waist=0.3).astype(np.complex128)
+    E_sites, _ = OS.tt_svd(OQ.dense_to_quantics(E, "interleaved"), n, 4, 64, 1e-14)
+    mx, my = synth.smooth_random_phase_mask_factors(n, seed=932, strength=0.5)
+    X, _ = OS.tt_svd(mx, n, 2, 64, 1e-14)
+    Y, _ = OS.tt_svd(my, n, 2, 64, 1e-14)
+    M_sites = OS.kron_interleave(X, Y)
+    It = OQ.dense_to_quantics(synth.rectangles_target(n, seed=933).astype(np.float64), "interleaved")
+    Q = OM.qft_mpo_layers(n, 1e-14)
+    ops = (Q, OM.dagger(Q), OM.phase_mpo(n, 0.5, 1e-14))
+    return OO, E_sites, M_sites, It, ops
+
+
+def test_frozen_adjoint_matches_finite_differences_of_the_frozen_map():
+    # with truncation active (chi 6 < the 4^2 bond of n = 4) the adjoint is the exact derivative of the map with
+    # the recorded projectors held fixed: central differences along random directions
+    n = 4
+    OO, E_sites, M_sites, It, ops = _frozen_case(n, 6)
+    L, G, pieces = OO.frozen_loss_and_grad(E_sites, M_sites, It, n, ops, 6, 0.0)
+    m = OS.to_vector(M_sites)
+    assert abs(OO.frozen_loss(m, pieces, It) - L) < 1e-12 * L
+    rng = np.random.default_rng(3)
+    for _ in range(4):
+        dm = rng.standard_normal(m.shape) + 1j * rng.standard_normal(m.shape)
+        h = 1e-6
+        fd = (OO.frozen_loss(m + h * dm, pieces, It) - OO.frozen_loss(m - h * dm, pieces, It)) / (2 * h)
+        assert abs(fd - 2 * np.real(np.vdot(G, dm))) < 1e-6 * np.abs(fd) + 1e-9
+
+
+def test_frozen_adjoint_with_full_frames_is_the_true_gradient():
+    # n = 2: every frame spans the whole space (bonds 4 = d), so every projector is the identity and the frozen
+    # gradient is the dense gradient of the loss
+    n = 2
+    OO, E_sites, M_sites, It, ops = _frozen_case(n, 64)
+    L, G, (P, K, e) = OO.frozen_loss_and_grad(E_sites, M_sites, It, n, ops, 64, 0.0)
+    assert all(np.allclose(Pi, np.eye(16), atol=1e-12) for Pi in P)
+    Ed = OQ.quantics_to_dense(OS.to_vector(E_sites), n, "interleaved")
+    Md = OQ.quantics_to_dense(OS.to_vector(M_sites), n, "interleaved")
+    Itd = OQ.quantics_to_dense(It, n, "interleaved")
+    ref = OO.intensity_loss_grad_dense(Ed, Md, Itd, 0.5)
+    assert abs(L - OO.intensity_loss_dense(Ed, Md, Itd, 0.5)) < 1e-9 * L
+    assert np.linalg.norm(OQ.quantics_to_dense(G, n, "interleaved") - ref) < 1e-9 * np.linalg.norm(ref)
