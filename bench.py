@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--workload", choices=["fresnel", "batched", "optics"], default="fresnel",
                     help="batched: many independent wavefronts (n 8-12, chi 16-64) stepped as CUDA graphs")
     ap.add_argument("--items", type=int, default=64, help="items of the batched workload")
+    ap.add_argument("--branches", type=int, default=0, help="parallel branches of the batched graph (0: auto)")
     ap.add_argument("--oracle-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--oracle-budget", type=float, default=30.0, help=argparse.SUPPRESS)
     args = ap.parse_args()
@@ -304,20 +305,21 @@ def run_ours(args, rank, ws, local, prec):
 
 def run_batched(args, local):
     """Independent wavefronts of the batched workload (Gaussian beam x Kolmogorov phase screen, n in 8..12,
-    chi in {16, 32, 64}), each on its own stream, one CUDA graph per item per step."""
+    chi in {16, 32, 64}), all advanced by one launch of one CUDA graph per step (the items split into parallel
+    branches), with the GEMM tile of each (n, chi) class chosen by the autotuner on a copy of one of its items."""
     import torch
     import synth
     from paper_2510_23089_gb300 import qtn
 
     torch.cuda.set_device(local)
+    prec = "fp32" if args.prec == "fp32" else "mixed"
     specs = synth.batched_item_specs(count=args.items)
     nmax, cmax = max(s["n"] for s in specs), max(s["chi"] for s in specs)
     enc = qtn.Engine(n_sites=nmax, d=4, chi=cmax, w=16, dense=1 << (2 * nmax))
     ops = {}
     for n in sorted({s["n"] for s in specs}):
         Q = enc.build_qft_mpo(n, False, 1e-12, w_cap=16)
-        eng_p = qtn.Engine(n_sites=n, d=2, chi=16, w=2, dense=1 << n)
-        ops[n] = (Q, enc.mpo_dagger(Q), eng_p.build_phase_mpo(n, LAMBDA_Z_OVER_DX2 / (1 << n), 1e-12, w_cap=16))
+        ops[n] = (Q, enc.mpo_dagger(Q), enc.build_phase_mpo(n, LAMBDA_Z_OVER_DX2 / (1 << n), 1e-12, w_cap=16))
     items, engines = [], []
     for sp in specs:
         psi = qtn.MPS(sp["n"], 4, sp["chi"])
@@ -328,33 +330,48 @@ def run_batched(args, local):
         engines.append(qtn.Engine(n_sites=sp["n"], d=4, chi=sp["chi"], w=16, dense=0, stream=torch.cuda.Stream()))
     del enc
     torch.cuda.synchronize()
-    batch = qtn.Batch(engines, items, [ops[s["n"]][0] for s in specs], [ops[s["n"]][1] for s in specs],
-                      [ops[s["n"]][2] for s in specs], n_steps=1, chi_max=cmax, cutoff=args.cutoff)
-    batch.launch(args.warmup)
+    # autotuner: GEMM tile per (n, chi) class, on a copy of the first item of the class (cached by QTN_TUNE_CACHE)
+    tiles = {}
+    for i, sp in enumerate(specs):
+        key = (sp["n"], sp["chi"])
+        if key not in tiles:
+            Q, Qd, D = ops[sp["n"]]
+            tiles[key] = engines[i].tune_gemm_tile(items[i].clone(), Q, Qd, D, sp["chi"], args.cutoff, prec)
+        engines[i].set_gemm_tile(tiles[key][0])
     torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
+    Qs, Qds, Ds = [ops[s["n"]][0] for s in specs], [ops[s["n"]][1] for s in specs], [ops[s["n"]][2] for s in specs]
+    branches, tuned_ms = args.branches, None
+    if branches <= 0:   # autotuner: parallel branches of the graph, on copies of the items
+        copies = [it.clone() for it in items]
+        cands = sorted({max(1, args.items // 4), max(1, args.items // 2), args.items})
+        branches, tuned_ms = qtn.tune_branches(engines, copies, Qs, Qds, Ds, 0, args.cutoff, prec, cands)
+        del copies
+    t0 = time.perf_counter()
+    batch = qtn.Batch(engines, items, Qs, Qds, Ds, n_steps=1, chi_max=0, cutoff=args.cutoff, prec=prec,
+                      branches=branches)
+    build_s = time.perf_counter() - t0
+    stream = batch.stream
+    batch.launch(args.warmup)
+    batch.sync()
     sampler = ClockSampler(local)
     launches0 = qtn.load_library().qtn_launch_count()
     sampler.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for eng in engines:   # every item stream starts after e0
-        eng.stream.wait_event(e0)
     batch.launch(args.steps)
-    for eng in engines:
-        ev = torch.cuda.Event()
-        ev.record(eng.stream)
-        stream.wait_event(ev)
     e1.record(stream)
     e1.synchronize()
     ms = e0.elapsed_time(e1)
     clocks = sampler.stop()
     launches = qtn.load_library().qtn_launch_count() - launches0
+    batch.sync()
     batch.close()
     hist = {}
     for s in specs:
         hist[f"n{s['n']}_chi{s['chi']}"] = hist.get(f"n{s['n']}_chi{s['chi']}", 0) + 1
-    return {"ms": ms, "clocks": clocks, "launches": launches, "hist": hist}
+    return {"ms": ms, "clocks": clocks, "launches": launches, "hist": hist, "prec": prec, "build_s": build_s,
+            "branches": branches, "branches_tuned_ms": tuned_ms,
+            "tiles": {f"n{k[0]}_chi{k[1]}": {"tile": v[0], "ms_per_step_one_item": v[1]} for k, v in tiles.items()}}
 
 
 def run_optics(args, local):
@@ -582,12 +599,15 @@ def main():
         value = args.items * args.steps * ws / (r["ms"] / 1e3)
         line = {"metric": "batched Fresnel MPO-MPS item-steps/s", "value": value, "unit": "item-steps/s",
                 "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp32",
-                "data": "synthetic",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "fp32" if r["prec"] == "fp32" else "bf16", "data": "synthetic",
                 "config": {"workload": f"{args.items} interleaved wavefronts, Gaussian beam x Kolmogorov phase screen, "
-                                       "n in 8..12, chi in {16,32,64}, one CUDA graph per item on its own stream",
+                                       "n in 8..12, chi in {16,32,64}, one CUDA graph of all items launched once per "
+                                       "step", "precision": r["prec"], "gemm_tiles_autotuned": r["tiles"],
+                           "branches_autotuned": {"branches": r["branches"], "ms_per_step": r["branches_tuned_ms"]},
+                           "graph_build_s": r["build_s"],
                            "items": r["hist"], "cutoff": args.cutoff, "parallelism": f"replicas x{ws}",
-                           "l2": "items stay L2-resident (no flush): the batch is one launch of all graphs"},
+                           "l2": "items stay L2-resident (no flush): the batch is one launch of one graph"},
                 "clocks": r["clocks"], "gpu_launches": r["launches"], "e2e": None, "roofline": None}
         if rank == 0:
             print(json.dumps(line), flush=True)

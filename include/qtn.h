@@ -290,25 +290,62 @@ qtn_status qtn_add(void* ctx, const qtn_mps* a, const qtn_mps* b, qtn_mps* out);
 
 /* Batched Fresnel steps over many independent interleaved wavefronts (the
  * data-parallel execution of Sec. VI.A over a batch; the paper treats one field
- * at a time).  Item i is advanced on its own context ctxs[i] (its own stream,
- * not the legacy default stream) with its own workspace ws[i] and operators
- * qft[i], qft_dagger[i], phase[i] (arrays of count; items may differ in n and
- * chi).  qtn_batch_create records n_steps steps of every item into one CUDA
- * graph per item without running them; qtn_batch_launch(batch, k) launches
- * every item's graph k times, so the items run concurrently across the GPU.
- * Items must be in a canonical form (LEFT or RIGHT, as qtn_encode and
- * qtn_truncate leave them): QTN_CANON_NONE returns QTN_ERR_ARG.
- * The items, operators and workspaces must stay allocated and unmoved while
- * the batch exists; profiling must be off; statistics are not collected (use
- * qtn_norm2 / qtn_overlap afterwards, and qtn_batch_sync for the status). */
+ * at a time).  Item i has its own context ctxs[i] (its own created stream, not
+ * the legacy default stream), workspace ws[i] and operators qft[i],
+ * qft_dagger[i], phase[i] (arrays of count; items may differ in n and chi).
+ * qtn_batch_create records n_steps steps of every item into ONE CUDA graph
+ * without running them: the items are split into `branches` parallel branches
+ * (<= 0: one per item), assigned longest-first by the cost n chi^3 of a step
+ * to the least loaded branch, each branch running its items one after the
+ * other on the stream of one of the first `branches` contexts (those streams
+ * must be distinct); the branches fork from and join into the first context's
+ * stream.  qtn_batch_launch(batch, k) launches that graph k times on that
+ * stream (qtn_batch_stream returns it), so all items advance concurrently in
+ * one launch.  Each item truncates to min(trunc.chi_max, its chi_cap) (its
+ * chi_cap when chi_max <= 0) and uses its context's GEMM tile
+ * (qtn_set_gemm_tile, qtn_tune_gemm_tile).  Items must be in a canonical form (LEFT or RIGHT, as
+ * qtn_encode and qtn_truncate leave them): QTN_CANON_NONE returns QTN_ERR_ARG.
+ * The items, operators, workspaces and streams must stay allocated and unmoved
+ * while the batch exists; profiling must be off; statistics are not collected
+ * (use qtn_norm2 / qtn_overlap afterwards, and qtn_batch_sync for the status). */
 qtn_status qtn_batch_create(int count, void* const* ctxs, qtn_mps* items, const qtn_mpo* qft,
                             const qtn_mpo* qft_dagger, const qtn_mpo* phase, int n_steps, qtn_trunc trunc,
-                            void* const* ws, const size_t* ws_bytes, void** batch);
+                            void* const* ws, const size_t* ws_bytes, int branches, void** batch);
 qtn_status qtn_batch_launch(void* batch, int repeats);
-/* Waits for every item's stream and returns the most severe failure any
- * item's replays raised since the last qtn_batch_sync (as qtn_check). */
+/* The stream the batch's graph is launched on (cudaStream_t as void*). */
+qtn_status qtn_batch_stream(void* batch, void** stream);
+/* Waits for the batch and returns the most severe failure any item's replays
+ * raised since the last qtn_batch_sync (as qtn_check). */
 qtn_status qtn_batch_sync(void* batch);
 qtn_status qtn_batch_destroy(void* batch);
+
+/* Autotuner of the batch's launch shape: for each of the n_candidates branch
+ * counts, records a one-step batch (qtn_batch_create), launches it once as
+ * warm-up and once timed, and returns the fastest count (best_out, and its ms
+ * per step in ms_out when non-NULL).  Cached like qtn_tune_gemm_tile, keyed by
+ * the device, the item count and the (n, chi) multiset of the items.  The items
+ * are advanced by the trial steps (tune on copies).  Synchronises. */
+qtn_status qtn_batch_tune_branches(int count, void* const* ctxs, qtn_mps* items, const qtn_mpo* qft,
+                                   const qtn_mpo* qft_dagger, const qtn_mpo* phase, qtn_trunc trunc,
+                                   void* const* ws, const size_t* ws_bytes, const int* candidates,
+                                   int n_candidates, const char* cache_path, int* best_out, double* ms_out);
+
+/* Tile of the generic complex GEMM for the launches of a context: 64 (64 x 64
+ * outputs per CTA, the default) or 32 (32 x 32: four times the CTAs on the
+ * small contractions of low-chi items).  QTN_ERR_ARG for any other value. */
+qtn_status qtn_set_gemm_tile(void* ctx, int tile);
+
+/* Autotuner of the GEMM tile: times one Fresnel step of `item` (after one step
+ * of warm-up) with each tile, keeps the faster for the context and returns it
+ * (tile_out, and its ms per step in ms_out when non-NULL).  The decision is
+ * cached in a text file, one line "<key> <tile> <ms>" per workload class (device
+ * name, n, d, chi capacity, operator bond, chi_max, precision), at cache_path,
+ * or at $QTN_TUNE_CACHE when cache_path is NULL (no caching when both are
+ * absent); a cached class is not timed again.  The item is advanced by the
+ * trial steps (tune on a copy).  Synchronises. */
+qtn_status qtn_tune_gemm_tile(void* ctx, qtn_mps* item, const qtn_mpo* qft, const qtn_mpo* qft_dagger,
+                              const qtn_mpo* phase, qtn_trunc trunc, void* ws, size_t ws_bytes,
+                              const char* cache_path, int* tile_out, double* ms_out);
 
 /* Elementwise (Hadamard) product of two MPS in the same site basis (Sec. V,
  * Eq. psf_eq: the local product of physical legs, O(d chi^3) per site):

@@ -23,7 +23,10 @@
 namespace qtn {
 
 // ------------------------------------------------------------------ GEMM
-constexpr int GB_M = 64, GB_N = 64, GB_K = 16, G_THREADS = 256;
+// Tiles of TM x TN outputs, 256 threads each holding RM x RN accumulators, K staged 16 at a time through shared
+// memory.  Two shapes: 64 x 64 (the default) and 32 x 32 (four times the CTAs on the small contractions of
+// chi <= 32 items, where a 64-wide tile leaves most of its threads idle); the batch tuner picks per workload.
+constexpr int GB_K = 16, G_THREADS = 256;
 
 __device__ __forceinline__ float2 mat_get(const Mat& m, int i, int j, long long rs, long long cs, int jdiv,
                                           long long cs_hi) {
@@ -34,10 +37,12 @@ __device__ __forceinline__ float2 mat_get(const Mat& m, int i, int j, long long 
     return m.conj ? cconj(v) : v;
 }
 
-__global__ void __launch_bounds__(G_THREADS) k_gemm(GemmDesc d, const int* __restrict__ R) {
+template <int TM, int TN, int RM, int RN>
+__global__ void __launch_bounds__(G_THREADS) k_gemm_t(GemmDesc d, const int* __restrict__ R) {
+    static_assert((TM / RM) * (TN / RN) == G_THREADS, "one accumulator block per thread");
     if (d.guard_reg >= 0 && R[d.guard_reg] != d.guard_val) return;
     const int M = d.M.eval(R), N = d.N.eval(R), K = d.K.eval(R);
-    const int m0 = blockIdx.y * GB_M, n0 = blockIdx.x * GB_N;
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
     if (m0 >= M || n0 >= N) return;
     int k_begin = 0, k_end = K;
     if (d.mode == OUT_ATOMIC64) {
@@ -52,33 +57,31 @@ __global__ void __launch_bounds__(G_THREADS) k_gemm(GemmDesc d, const int* __res
     const bool a_kfast = (acs == 1);   // K contiguous in A: let consecutive threads walk K
     const bool b_nfast = (bcs == 1);
 
-    __shared__ float2 As[GB_K][GB_M + 1];
-    __shared__ float2 Bs[GB_K][GB_N + 1];
+    __shared__ float2 As[GB_K][TM + 1];
+    __shared__ float2 Bs[GB_K][TN + 1];
     const int tid = threadIdx.x;
-    const int ty = tid / 16, tx = tid % 16;
-    float2 acc[4][4];
+    const int ty = tid / (TN / RN), tx = tid % (TN / RN);
+    float2 acc[RM][RN];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < RM; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
+        for (int b = 0; b < RN; ++b) acc[a][b] = make_float2(0.f, 0.f);
 
     for (int k0 = k_begin; k0 < k_end; k0 += GB_K) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            int e = tid + q * G_THREADS;
+        for (int e = tid; e < GB_K * TM; e += G_THREADS) {
             int ii, kk;
-            if (a_kfast) { ii = e / GB_K; kk = e % GB_K; } else { ii = e % GB_M; kk = e / GB_M; }
-            int gi = m0 + ii, gk = k0 + kk;
+            if (a_kfast) { ii = e / GB_K; kk = e % GB_K; } else { ii = e % TM; kk = e / TM; }
+            const int gi = m0 + ii, gk = k0 + kk;
             float2 v = make_float2(0.f, 0.f);
             if (gi < M && gk < k_end) v = mat_get(d.A, gi, gk, ars, acs, ajd, ach);
             As[kk][ii] = v;
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            int e = tid + q * G_THREADS;
+        for (int e = tid; e < GB_K * TN; e += G_THREADS) {
             int jj, kk;
-            if (b_nfast) { jj = e % GB_N; kk = e / GB_N; } else { jj = e / GB_K; kk = e % GB_K; }
-            int gj = n0 + jj, gk = k0 + kk;
+            if (b_nfast) { jj = e % TN; kk = e / TN; } else { jj = e / GB_K; kk = e % GB_K; }
+            const int gj = n0 + jj, gk = k0 + kk;
             float2 v = make_float2(0.f, 0.f);
             if (gj < N && gk < k_end) {
                 if (d.omega_seed >= 0) v = gauss2(d.omega_seed, gk, gj);
@@ -89,32 +92,32 @@ __global__ void __launch_bounds__(G_THREADS) k_gemm(GemmDesc d, const int* __res
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < GB_K; ++kk) {
-            float2 av[4], bv[4];
+            float2 av[RM], bv[RN];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) av[a] = As[kk][ty * 4 + a];
+            for (int a = 0; a < RM; ++a) av[a] = As[kk][ty * RM + a];
 #pragma unroll
-            for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx * 4 + b];
+            for (int b = 0; b < RN; ++b) bv[b] = Bs[kk][tx * RN + b];
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < RM; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) cfma(acc[a][b], av[a], bv[b]);
+                for (int b = 0; b < RN; ++b) cfma(acc[a][b], av[a], bv[b]);
         }
         __syncthreads();
     }
     if (d.flops != nullptr && threadIdx.x == 0)
-        atomicAdd(d.flops, 8.0 * (double)min(GB_M, M - m0) * (double)min(GB_N, N - n0) * (double)(k_end - k_begin));
+        atomicAdd(d.flops, 8.0 * (double)min(TM, M - m0) * (double)min(TN, N - n0) * (double)(k_end - k_begin));
     const long long crs = d.crs.eval(R), ccs = d.ccs.eval(R);
     const float2 alpha = make_float2(d.alpha_re, d.alpha_im);
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        int gi = m0 + ty * 4 + a;
+    for (int a = 0; a < RM; ++a) {
+        const int gi = m0 + ty * RM + a;
         if (gi >= M) continue;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            int gj = n0 + tx * 4 + b;
+        for (int b = 0; b < RN; ++b) {
+            const int gj = n0 + tx * RN + b;
             if (gj >= N) continue;
-            float2 v = cmul(alpha, acc[a][b]);
-            long long off = (long long)gi * crs + (long long)gj * ccs;
+            const float2 v = cmul(alpha, acc[a][b]);
+            const long long off = (long long)gi * crs + (long long)gj * ccs;
             if (d.mode == OUT_STORE) {
                 ((float2*)d.C)[off] = v;
             } else if (d.mode == OUT_ACCUM) {
@@ -129,9 +132,15 @@ __global__ void __launch_bounds__(G_THREADS) k_gemm(GemmDesc d, const int* __res
     }
 }
 
+// GEMM tile of the launches made by the calling host thread (set per context by the entry points).
+static thread_local int t_gemm_tile = 64;
+void set_gemm_tile(int tile) { t_gemm_tile = (tile == 32) ? 32 : 64; }
+int gemm_tile() { return t_gemm_tile; }
+
 cudaError_t launch_gemm(const GemmDesc& d, int max_m, int max_n, int max_k, const int* R, cudaStream_t s) {
     if (max_m <= 0 || max_n <= 0) return cudaSuccess;
-    dim3 grid((max_n + GB_N - 1) / GB_N, (max_m + GB_M - 1) / GB_M, 1);
+    const int T = t_gemm_tile;
+    dim3 grid((max_n + T - 1) / T, (max_m + T - 1) / T, 1);
     if (d.mode == OUT_ATOMIC64) {
         int kc = d.kchunk > 0 ? d.kchunk : 1;
         grid.z = (unsigned)((max(max_k, 1) + kc - 1) / kc);
@@ -139,7 +148,8 @@ cudaError_t launch_gemm(const GemmDesc& d, int max_m, int max_n, int max_k, cons
     GemmDesc dd = d;
     if (g_prof_ledger) dd.flops = g_prof_ledger + L_PROF_GEMM;
     count_launch(PROF_GEMM, s, true);
-    k_gemm<<<grid, G_THREADS, 0, s>>>(dd, R);
+    if (T == 32) k_gemm_t<32, 32, 2, 2><<<grid, G_THREADS, 0, s>>>(dd, R);
+    else k_gemm_t<64, 64, 4, 4><<<grid, G_THREADS, 0, s>>>(dd, R);
     count_launch(PROF_GEMM, s, false);
     return cudaGetLastError();
 }

@@ -10,23 +10,29 @@
 // [hi, hi, lo] against B segments [hi, lo, hi].  A plain BF16 product (one segment) misses the 3e-3 budget of
 // a Fresnel step; the split keeps the step within FP32 rounding of the plain path.
 //
-// One CTA computes a 128 x 128 tile of the real result (64 complex rows x 128 columns) in TMEM.  Its four
-// warps convert their share of each 64-wide K chunk of A and B from the strided complex operands straight into
-// shared memory in the canonical no-swizzle K-major layout (8 x 16-byte core matrices; 128 bytes between core
-// matrices along K, 1024 bytes between 8-row groups), fence the writes to the async proxy, and one thread
-// issues four tcgen05.mma (M = 128, N = 128, K = 16) per chunk and commits them to an mbarrier.  Two stages:
-// the warps convert chunk c + 1 while the tensor cores run chunk c.  Every mbarrier wait is bounded; a wait
-// that gives up raises the timeout flag, drains what is in flight (bounded again), frees TMEM and returns.
+// The operands are packed once per GEMM (k_pack_a, k_pack_b: every complex element read once, its six BF16
+// entries written straight into 128 x 64 tiles in the canonical no-swizzle K-major layout of the tensor
+// cores: 8 x 16-byte core matrices, 128 bytes apart along K and 1024 bytes apart between 8-row groups).  One
+// CTA of k_gemm_tc computes a 128 x 128 tile of the real result (64 complex rows x 128 columns) in tensor
+// memory: one thread streams the A and B tiles of each 64-wide K chunk into shared memory with cp.async.bulk
+// (16 KB each, completion on an mbarrier), four stages deep, and issues four tcgen05.mma (M = 128, N = 128,
+// K = 16) per chunk, committed to the stage's mbarrier so the stage is refilled as soon as its MMAs have read
+// it.  The four warps then read the accumulator with tcgen05.ld and write complex FP32 results.  Every
+// mbarrier wait is bounded; a wait that gives up raises the timeout flag, drains what is in flight (bounded
+// again), frees the tensor memory and returns.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 #include <math.h>
 
 #include "qtn_internal.cuh"
 
 namespace qtn {
 
-constexpr int TC_M = 128, TC_N = 128, TC_KC = 64, TC_THREADS = 128;
-constexpr int TC_TILE_ELEMS = TC_M * TC_KC;                              // bf16 per operand tile per stage
-constexpr size_t TC_SMEM = 2 * 2 * (size_t)TC_TILE_ELEMS * sizeof(__nv_bfloat16) + 1024;   // + alignment slack
+constexpr int TC_M = 128, TC_N = 128, TC_KC = 64, TC_THREADS = 128, TC_STAGES = 4;
+constexpr int TC_TILE_ELEMS = TC_M * TC_KC;                               // bf16 per operand tile
+constexpr uint32_t TC_TILE_BYTES = TC_TILE_ELEMS * 2;                     // 16 KB
+constexpr size_t TC_SMEM = 2 * TC_STAGES * (size_t)TC_TILE_BYTES + 1024;   // A and B stages + alignment slack
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 20;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -58,6 +64,14 @@ __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
     }
     return false;
 }
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
 
 __device__ __forceinline__ float2 tc_get(const Mat& m, int i, int j, long long rs, long long cs, int jdiv,
                                          long long cs_hi) {
@@ -68,35 +82,96 @@ __device__ __forceinline__ float2 tc_get(const Mat& m, int i, int j, long long r
     return m.conj ? make_float2(v.x, -v.y) : v;
 }
 
-__device__ __forceinline__ __nv_bfloat16 split_part(float v, int lo) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    return lo ? __float2bfloat16_rn(v - __bfloat162float(h)) : h;
+__device__ __forceinline__ void split2(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(v);
+    lo = __float2bfloat16_rn(v - __bfloat162float(hi));
 }
 
-__global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(GemmDesc d, int* R) {
+// K padded per half-segment to whole 64-wide chunks (a chunk never straddles a half-segment).
+__device__ __forceinline__ int tc_kp(int K) { return ((K + TC_KC - 1) / TC_KC) * TC_KC; }
+
+// A'' tiles: rows 2i, 2i+1 of complex row i; chunk c = seg * 2 cps + half * cps + k / 64 with segments
+// [hi, hi, lo] and halves [Ar | -Ai] (row 2i), [Ai | Ar] (row 2i+1).  Tile (mt, c) at (mt * nkc + c) tiles.
+__global__ void k_pack_a(GemmDesc d, const int* __restrict__ R, __nv_bfloat16* __restrict__ out, int nkc) {
+    if (d.guard_reg >= 0 && R[d.guard_reg] != d.guard_val) return;
+    const int M = d.M.eval(R), K = d.K.eval(R);
+    const int Kp = tc_kp(K), cps = Kp / TC_KC;
+    const long long ars = d.A.rs.eval(R), acs = d.A.cs.eval(R), ach = d.A.cs_hi.eval(R);
+    const int ajd = d.A.jdiv.eval(R);
+    const bool kfast = (acs == 1);
+    const long long total = (long long)M * Kp;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = kfast ? (int)(e / Kp) : (int)(e % M), k = kfast ? (int)(e % Kp) : (int)(e / M);
+        float2 a = make_float2(0.f, 0.f);
+        if (k < K) a = tc_get(d.A, i, k, ars, acs, ajd, ach);
+        const int mt = (2 * i) / TC_M, r = (2 * i) % TC_M, kk = k % TC_KC, kb = k / TC_KC;
+        __nv_bfloat16 rh, rl, ih, il, nh, nl;
+        split2(a.x, rh, rl);
+        split2(a.y, ih, il);
+        split2(-a.y, nh, nl);
+        for (int seg = 0; seg < 3; ++seg)
+            for (int half = 0; half < 2; ++half) {
+                const int c = seg * 2 * cps + half * cps + kb;
+                __nv_bfloat16* t = out + ((long long)mt * nkc + c) * TC_TILE_ELEMS;
+                const bool lo = (seg == 2);
+                // half 0: row 2i Re, row 2i+1 Im;  half 1: row 2i -Im, row 2i+1 Re
+                t[tc_off(r, kk)] = half ? (lo ? nl : nh) : (lo ? rl : rh);
+                t[tc_off(r + 1, kk)] = half ? (lo ? rl : rh) : (lo ? il : ih);
+            }
+    }
+}
+
+// B'' tiles (stored as N rows x K): segments [hi, lo, hi], halves [Re B | Im B].  Tile (nt, c) at (nt * nkc + c).
+__global__ void k_pack_b(GemmDesc d, const int* __restrict__ R, __nv_bfloat16* __restrict__ out, int nkc) {
+    if (d.guard_reg >= 0 && R[d.guard_reg] != d.guard_val) return;
+    const int N = d.N.eval(R), K = d.K.eval(R);
+    const int Kp = tc_kp(K), cps = Kp / TC_KC;
+    const long long brs = d.B.rs.eval(R), bcs = d.B.cs.eval(R), bch = d.B.cs_hi.eval(R);
+    const int bjd = d.B.jdiv.eval(R);
+    const bool nfast = (bcs == 1);
+    const long long total = (long long)N * Kp;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int j = nfast ? (int)(e % N) : (int)(e / Kp), k = nfast ? (int)(e / N) : (int)(e % Kp);
+        float2 b = make_float2(0.f, 0.f);
+        if (k < K) b = tc_get(d.B, k, j, brs, bcs, bjd, bch);
+        const int nt = j / TC_N, r = j % TC_N, kk = k % TC_KC, kb = k / TC_KC;
+        __nv_bfloat16 rh, rl, ih, il;
+        split2(b.x, rh, rl);
+        split2(b.y, ih, il);
+        for (int seg = 0; seg < 3; ++seg)
+            for (int half = 0; half < 2; ++half) {
+                const int c = seg * 2 * cps + half * cps + kb;
+                const bool lo = (seg == 1);
+                out[((long long)nt * nkc + c) * TC_TILE_ELEMS + tc_off(r, kk)] = half ? (lo ? il : ih) : (lo ? rl : rh);
+            }
+    }
+}
+
+__global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(GemmDesc d, int* R, const __nv_bfloat16* __restrict__ Apk,
+                                                        const __nv_bfloat16* __restrict__ Bpk, int nkc) {
     if (d.guard_reg >= 0 && R[d.guard_reg] != d.guard_val) return;
     const int M = d.M.eval(R), N = d.N.eval(R), K = d.K.eval(R);
     const int m0 = blockIdx.y * (TC_M / 2), n0 = blockIdx.x * TC_N;   // complex rows / columns of this tile
     if (m0 >= M || n0 >= N) return;
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
-    __nv_bfloat16* smem = (__nv_bfloat16*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
-    __nv_bfloat16* sA[2] = {smem, smem + TC_TILE_ELEMS};
-    __nv_bfloat16* sB[2] = {smem + 2 * TC_TILE_ELEMS, smem + 3 * TC_TILE_ELEMS};
-    __shared__ __align__(8) uint64_t bar[2];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_s, issued_s;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const long long ars = d.A.rs.eval(R), acs = d.A.cs.eval(R), brs = d.B.rs.eval(R), bcs = d.B.cs.eval(R);
-    const int ajd = d.A.jdiv.eval(R), bjd = d.B.jdiv.eval(R);
-    const long long ach = d.A.cs_hi.eval(R), bch = d.B.cs_hi.eval(R);
-    const bool a_kfast = (acs == 1), b_nfast = (bcs == 1);
-    const int Kp = ((K + TC_KC - 1) / TC_KC) * TC_KC;   // K padded per half-segment: a chunk never straddles one
-    const int cps = Kp / TC_KC;                          // chunks per half-segment
-    const int nch = 6 * cps;                             // 3 segments x 2 halves
+    const int nch = 6 * (tc_kp(K) / TC_KC);   // 3 segments x 2 halves x chunks per half
+    const __nv_bfloat16* Ab = Apk + (long long)blockIdx.y * nkc * TC_TILE_ELEMS;
+    const __nv_bfloat16* Bb = Bpk + (long long)blockIdx.x * nkc * TC_TILE_ELEMS;
+    auto sA = [&](int st) { return smem + (size_t)st * TC_TILE_BYTES; };
+    auto sB = [&](int st) { return smem + (size_t)(TC_STAGES + st) * TC_TILE_BYTES; };
 
     if (tid == 0) {
-        mbar_init(smem_u32(&bar[0]), 1);
-        mbar_init(smem_u32(&bar[1]), 1);
+        for (int st = 0; st < TC_STAGES; ++st) {
+            mbar_init(smem_u32(&full[st]), 1);
+            mbar_init(smem_u32(&empty[st]), 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_s = 0;
         issued_s = 0;
@@ -112,43 +187,20 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(GemmDesc d, int* R) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
 
-    for (int c = 0; c < nch; ++c) {
-        const int s = c & 1;
-        if (c >= 2) {   // stage s still feeds the MMAs of chunk c - 2
-            if (tid == 0 && !mbar_wait(smem_u32(&bar[s]), ((c - 2) >> 1) & 1)) abort_s = 1;
-            __syncthreads();
-            if (abort_s) break;
+    if (tid == 0) {
+        // prologue: fill the stages
+        for (int c = 0; c < nch && c < TC_STAGES; ++c) {
+            const uint32_t fb = smem_u32(&full[c]);
+            mbar_expect_tx(fb, 2 * TC_TILE_BYTES);
+            bulk_g2s(smem_u32(sA(c)), Ab + (long long)c * TC_TILE_ELEMS, TC_TILE_BYTES, fb);
+            bulk_g2s(smem_u32(sB(c)), Bb + (long long)c * TC_TILE_ELEMS, TC_TILE_BYTES, fb);
         }
-        const int seg = c / (2 * cps), half = (c / cps) & 1, kb = (c % cps) * TC_KC;
-        const int lo_a = (seg == 2), lo_b = (seg == 1);
-        // A'' rows 2i, 2i+1 of the 64 complex rows of this tile, k in [kb, kb + 64); consecutive threads walk the
-        // contiguous index of A
-        for (int e = tid; e < (TC_M / 2) * TC_KC; e += TC_THREADS) {
-            const int ir = a_kfast ? e / TC_KC : e % (TC_M / 2), kk = a_kfast ? e % TC_KC : e / (TC_M / 2);
-            const int i = m0 + ir, k = kb + kk;
-            float2 a = make_float2(0.f, 0.f);
-            if (i < M && k < K) a = tc_get(d.A, i, k, ars, acs, ajd, ach);
-            // half 0: [Ar | Ai] on (re, im) rows; half 1: [-Ai | Ar]
-            const float vr = half ? -a.y : a.x, vi = half ? a.x : a.y;
-            sA[s][tc_off(2 * ir, kk)] = split_part(vr, lo_a);
-            sA[s][tc_off(2 * ir + 1, kk)] = split_part(vi, lo_a);
-        }
-        // B'' (stored as N rows x K): half 0 Re B, half 1 Im B
-        for (int e = tid; e < TC_N * TC_KC; e += TC_THREADS) {
-            const int jr = b_nfast ? e % TC_N : e / TC_KC, kk = b_nfast ? e / TC_N : e % TC_KC;
-            const int j = n0 + jr, k = kb + kk;
-            float v = 0.f;
-            if (j < N && k < K) {
-                const float2 b = tc_get(d.B, k, j, brs, bcs, bjd, bch);
-                v = half ? b.y : b.x;
-            }
-            sB[s][tc_off(jr, kk)] = split_part(v, lo_b);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
+        int issued = 0;
+        for (int c = 0; c < nch; ++c) {
+            const int st = c % TC_STAGES, use = c / TC_STAGES;
+            if (!mbar_wait(smem_u32(&full[st]), use & 1)) { abort_s = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = smem_u32(sA[s]), b0 = smem_u32(sB[s]);
+            const uint32_t a0 = smem_u32(sA(st)), b0 = smem_u32(sB(st));
 #pragma unroll
             for (int kk = 0; kk < TC_KC / 16; ++kk) {
                 const uint64_t ad = tc_desc(a0 + 256 * kk), bd = tc_desc(b0 + 256 * kk);
@@ -160,16 +212,28 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(GemmDesc d, int* R) {
                     : "memory");
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&bar[s]))
+                             smem_u32(&empty[st]))
                          : "memory");
-            issued_s = c + 1;   // read by the other threads only after the next barrier
+            issued = c + 1;
+            const int cn = c + TC_STAGES;   // refill this stage once its MMAs have read it
+            if (cn < nch) {
+                if (!mbar_wait(smem_u32(&empty[st]), use & 1)) { abort_s = 1; break; }
+                const uint32_t fb = smem_u32(&full[st]);
+                mbar_expect_tx(fb, 2 * TC_TILE_BYTES);
+                bulk_g2s(smem_u32(sA(st)), Ab + (long long)cn * TC_TILE_ELEMS, TC_TILE_BYTES, fb);
+                bulk_g2s(smem_u32(sB(st)), Bb + (long long)cn * TC_TILE_ELEMS, TC_TILE_BYTES, fb);
+            }
         }
-    }
-    // wait for the last commit (it covers every MMA issued before it); after a timeout, wait (bounded) for what
-    // was issued so the tensor memory is no longer written when it is freed
-    if (tid == 0 && issued_s > 0) {
-        const int cl = issued_s - 1;
-        if (!mbar_wait(smem_u32(&bar[cl & 1]), (cl >> 1) & 1)) abort_s = 1;
+        // the last commit covers every MMA issued before it
+        if (issued > 0) {
+            const int cl = issued - 1;
+            if (!mbar_wait(smem_u32(&empty[cl % TC_STAGES]), (cl / TC_STAGES) & 1)) abort_s = 1;
+        }
+        // after a timeout, let the bulk copies already issued land (bounded) before the CTA leaves
+        if (abort_s)
+            for (int c = issued; c < nch && c < issued + TC_STAGES; ++c)
+                mbar_wait(smem_u32(&full[c % TC_STAGES]), (c / TC_STAGES) & 1);
+        issued_s = issued;
     }
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -219,16 +283,36 @@ cudaError_t configure_tc_kernel() {
     return cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
 }
 
-// Complex GEMM (STORE or ACCUM output, FP32) on the tensor cores; same descriptor as launch_gemm.
-cudaError_t launch_gemm_tc(const GemmDesc& d, int max_m, int max_n, int max_k, const int* R, cudaStream_t s) {
-    (void)max_k;
-    if (max_m <= 0 || max_n <= 0) return cudaSuccess;
+// Bytes of packed operands for a GEMM of capacity max_m x max_n x max_k.
+size_t tc_pack_bytes(int max_m, int max_n, int max_k) {
+    const size_t nkc = 6 * (size_t)((max_k + TC_KC - 1) / TC_KC);
+    const size_t mt = (size_t)(2 * max_m + TC_M - 1) / TC_M, nt = (size_t)(max_n + TC_N - 1) / TC_N;
+    return (mt + nt) * nkc * TC_TILE_BYTES;
+}
+
+// Complex GEMM (STORE or ACCUM output, FP32) on the tensor cores; same descriptor as launch_gemm.  `pack` holds
+// the packed operands (tc_pack_bytes of the capacities, 16-byte aligned).
+cudaError_t launch_gemm_tc(const GemmDesc& d, int max_m, int max_n, int max_k, const int* R, void* pack,
+                           size_t pack_bytes, int sm_count, cudaStream_t s) {
+    if (max_m <= 0 || max_n <= 0 || max_k <= 0) return cudaSuccess;
     if (d.mode == OUT_ATOMIC64 || d.omega_seed >= 0) return cudaErrorInvalidValue;
-    dim3 grid((max_n + TC_N - 1) / TC_N, (max_m + TC_M / 2 - 1) / (TC_M / 2), 1);
+    if (!pack || pack_bytes < tc_pack_bytes(max_m, max_n, max_k) || ((uintptr_t)pack & 15)) return cudaErrorInvalidValue;
+    const int nkc = 6 * ((max_k + TC_KC - 1) / TC_KC);
+    const int mt = (2 * max_m + TC_M - 1) / TC_M, nt = (max_n + TC_N - 1) / TC_N;
+    __nv_bfloat16* Apk = (__nv_bfloat16*)pack;
+    __nv_bfloat16* Bpk = Apk + (size_t)mt * nkc * TC_TILE_ELEMS;
+    const int kp = ((max_k + TC_KC - 1) / TC_KC) * TC_KC;
+    const long long na = (long long)max_m * kp, nb = (long long)max_n * kp;
+    auto blocks = [&](long long n) { return (int)std::max(1LL, std::min((n + 255) / 256, (long long)sm_count * 8)); };
+    k_pack_a<<<blocks(na), 256, 0, s>>>(d, R, Apk, nkc);
+    count_launch(PROF_OTHER, s, false);
+    k_pack_b<<<blocks(nb), 256, 0, s>>>(d, R, Bpk, nkc);
+    count_launch(PROF_OTHER, s, false);
+    dim3 grid(nt, mt, 1);
     GemmDesc dd = d;
     if (g_prof_ledger) dd.flops = g_prof_ledger + L_PROF_TC;
     count_launch(PROF_TC, s, true);
-    k_gemm_tc<<<grid, TC_THREADS, TC_SMEM, s>>>(dd, (int*)R);
+    k_gemm_tc<<<grid, TC_THREADS, TC_SMEM, s>>>(dd, (int*)R, Apk, Bpk, nkc);
     count_launch(PROF_TC, s, false);
     return cudaGetLastError();
 }

@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cmath>
 #include <mutex>
 #include <vector>
 
@@ -125,6 +126,9 @@ WsLayout ws_layout(int N, int d, int chi, int w, long long dense) {
     L.X0 = take(dn * c8);
     L.X1 = take(dn * c8);
     L.b64 = take(build64_scratch_bytes(std::max(N, 1)));   // FP64 operator builds
+    // packed operands of the tensor-core site contraction: (chi w) x (d chi) x chi at the capacities
+    L.tc_bytes = tc_pack_bytes(chi * std::max(w, 1), d * chi, chi);
+    L.tc = take(L.tc_bytes);
     L.total = off;
     return L;
 }
@@ -149,6 +153,7 @@ static Ws ws_bind(void* base, const WsLayout& L) {
     w.Z = (float2*)at(L.Z);
     w.X0 = (float2*)at(L.X0);
     w.X1 = (float2*)at(L.X1);
+    w.tc = at(L.tc);
     return w;
 }
 
@@ -500,7 +505,8 @@ qtn_status zip_pass(Ctx* c, Ws& w, qtn_mps* psi, const qtn_mpo* W, int axis, int
             g.M = dr(R_MID); g.N = dr(R_DN); g.K = dr(R_CHIL);
             g.mode = OUT_STORE; g.alpha_re = 1.f; g.omega_seed = -1;
             // the site contraction: split-BF16 tensor cores with FP32 accumulation in mixed precision
-            if (tr.prec == QTN_MIXED) CK(launch_gemm_tc(g, cap * wmax, d * cap, cap, w.R, s));
+            if (tr.prec == QTN_MIXED)
+                CK(launch_gemm_tc(g, cap * wmax, d * cap, cap, w.R, w.tc, w.L.tc_bytes, c->sm_count, s));
             else CK(launch_gemm(g, cap * wmax, d * cap, cap, w.R, s));
         }
         const float2* Wc = nullptr;
@@ -588,6 +594,7 @@ using namespace qtn;
 // ============================================================================ C ABI
 
 qtn_status bind_ws(qtn_context* x, void* ws, size_t bytes, Ws& w) {
+    set_gemm_tile(x->c.gemm_tile);
     if (!x->have_layout) return QTN_ERR_WORKSPACE;
     qtn_status st = check_ws(x->L, ws, bytes);
     if (st) return st;
@@ -661,6 +668,7 @@ qtn_status qtn_create(void** ctx, void* stream) {
         free(x);
         return QTN_ERR_CUDA;
     }
+    x->c.gemm_tile = 64;
     *ctx = x;
     return QTN_OK;
 }
@@ -1244,9 +1252,11 @@ qtn_status qtn_amplitudes(void* ctx, const qtn_mps* psi, const int* digits, int 
 }  // extern "C"
 
 struct qtn_batch {
-    std::vector<cudaGraphExec_t> exec;
-    std::vector<cudaStream_t> stream;
-    std::vector<int*> sticky;   // each item's sticky status word (in its workspace)
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t master = nullptr;
+    std::vector<cudaStream_t> stream;   // every item's stream (its status word is read on it)
+    std::vector<int*> sticky;           // each item's sticky status word (in its workspace)
+    int branches = 1;
     long long kernels_per_launch = 0;
 };
 
@@ -1254,51 +1264,102 @@ extern "C" {
 
 qtn_status qtn_batch_create(int count, void* const* ctxs, qtn_mps* items, const qtn_mpo* qft, const qtn_mpo* qft_dagger,
                             const qtn_mpo* phase, int n_steps, qtn_trunc trunc, void* const* ws,
-                            const size_t* ws_bytes, void** batch) {
+                            const size_t* ws_bytes, int branches, void** batch) {
     if (count < 1 || !ctxs || !items || !qft || !qft_dagger || !phase || !ws || !ws_bytes || !batch || n_steps < 1 ||
         !trunc_ok(trunc))
         return QTN_ERR_ARG;
-    qtn_batch* b = new qtn_batch;
-    qtn_status result = QTN_OK;
-    const long long launches0 = launch_total();
-    for (int i = 0; i < count && result == QTN_OK; ++i) {
+    if (branches <= 0) branches = count;
+    branches = std::max(1, std::min(branches, count));
+    std::vector<Ws> wss(count);
+    for (int i = 0; i < count; ++i) {
         qtn_context* x = (qtn_context*)ctxs[i];
-        if (!x || x->c.stream == nullptr) { result = QTN_ERR_ARG; break; }   // the legacy stream cannot be captured
-        Ws w;
-        if ((result = bind_ws(x, ws[i], ws_bytes[i], w))) break;
-        qtn_mps* psi = items + i;
+        if (!x || x->c.stream == nullptr) return QTN_ERR_ARG;   // the legacy stream cannot be captured
+        qtn_status st = bind_ws(x, ws[i], ws_bytes[i], wss[i]);
+        if (st) return st;
         // a graph replays the same passes every launch: the item must enter in the canonical form it leaves in
         // after a whole number of steps (an item with none would replay its canonicalisation sweep each time)
-        if (psi->canon == QTN_CANON_NONE) { result = QTN_ERR_ARG; break; }
-        const int canon0 = psi->canon;
-        const int naxes = 2;
-        const qtn_mpo* ops[3] = {qft + i, phase + i, qft_dagger + i};
-        cudaStream_t s = x->c.stream;
-        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) { result = QTN_ERR_CUDA; break; }
-        qtn_status st = QTN_OK;
-        k_reset_stats<<<1, 1, 0, s>>>(w.R, w.ledger);
-        count_launch(PROF_OTHER, 0, false);
-        for (int step = 0; step < n_steps && st == QTN_OK; ++step)
-            for (int o = 0; o < 3 && st == QTN_OK; ++o)
-                for (int ax = 0; ax < naxes && st == QTN_OK; ++ax) st = apply_inner(x, w, ops[o], ax, psi, trunc, false);
-        cudaGraph_t g = nullptr;
-        const cudaError_t ec = cudaStreamEndCapture(s, &g);
-        // capturing executed nothing: the item is unchanged, so is its canonical form
-        psi->canon = canon0;
-        if (st) { result = st; if (g) cudaGraphDestroy(g); break; }
-        if (ec != cudaSuccess || !g) { result = QTN_ERR_CUDA; break; }
-        cudaGraphExec_t e = nullptr;
-        const cudaError_t ei = cudaGraphInstantiate(&e, g, 0);
-        cudaGraphDestroy(g);
-        if (ei != cudaSuccess) { result = QTN_ERR_CUDA; break; }
-        b->exec.push_back(e);
-        b->stream.push_back(s);
-        b->sticky.push_back(w.R + R_STICKY);
+        if (items[i].canon == QTN_CANON_NONE) return QTN_ERR_ARG;
     }
+    // the branches run on the streams of the first `branches` items; they must be distinct
+    std::vector<cudaStream_t> bs(branches);
+    for (int g = 0; g < branches; ++g) {
+        bs[g] = ((qtn_context*)ctxs[g])->c.stream;
+        for (int h = 0; h < g; ++h)
+            if (bs[h] == bs[g]) return QTN_ERR_ARG;
+    }
+    // longest-processing-time assignment of items to branches by the cost of a step ~ n chi^3 (zip-up of chi-wide
+    // bonds over n sites)
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    auto cost = [&](int i) { return (double)items[i].n_sites * std::pow((double)items[i].chi_cap, 3.0); };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    std::vector<double> load(branches, 0.0);
+    std::vector<std::vector<int>> plan(branches);
+    for (int i : order) {
+        const int g = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        plan[g].push_back(i);
+        load[g] += cost(i);
+    }
+    qtn_batch* b = new qtn_batch;
+    b->master = bs[0];
+    b->branches = branches;
+    const long long launches0 = launch_total();
+    qtn_status result = QTN_OK;
+    std::vector<cudaEvent_t> ev(branches + 1, nullptr);
+    for (auto& e : ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) result = QTN_ERR_CUDA;
+    cudaGraph_t graph = nullptr;
+    if (result == QTN_OK && cudaStreamBeginCapture(b->master, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+        result = QTN_ERR_CUDA;
+    if (result == QTN_OK) {
+        // fork: every branch stream joins the capture after an event of the master stream
+        cudaEventRecord(ev[branches], b->master);
+        for (int g = 1; g < branches; ++g) cudaStreamWaitEvent(bs[g], ev[branches], 0);
+        for (int g = 0; g < branches && result == QTN_OK; ++g) {
+            for (int i : plan[g]) {
+                qtn_context* x = (qtn_context*)ctxs[i];
+                const cudaStream_t own = x->c.stream;
+                x->c.stream = bs[g];
+                set_gemm_tile(x->c.gemm_tile);
+                Ws& w = wss[i];
+                qtn_mps* psi = items + i;
+                const int canon0 = psi->canon;
+                const qtn_mpo* ops[3] = {qft + i, phase + i, qft_dagger + i};
+                // every item truncates to its own bond capacity (or chi_max, when smaller)
+                qtn_trunc ti = trunc;
+                ti.chi_max = (trunc.chi_max <= 0) ? psi->chi_cap : std::min(trunc.chi_max, psi->chi_cap);
+                k_reset_stats<<<1, 1, 0, bs[g]>>>(w.R, w.ledger);
+                count_launch(PROF_OTHER, 0, false);
+                qtn_status st = QTN_OK;
+                for (int step = 0; step < n_steps && st == QTN_OK; ++step)
+                    for (int o = 0; o < 3 && st == QTN_OK; ++o)
+                        for (int ax = 0; ax < 2 && st == QTN_OK; ++ax)
+                            st = apply_inner(x, w, ops[o], ax, psi, ti, false);
+                psi->canon = canon0;   // capturing executed nothing
+                x->c.stream = own;
+                if (st) { result = st; break; }
+            }
+        }
+        // join
+        for (int g = 1; g < branches; ++g) {
+            cudaEventRecord(ev[g], bs[g]);
+            cudaStreamWaitEvent(b->master, ev[g], 0);
+        }
+        const cudaError_t ec = cudaStreamEndCapture(b->master, &graph);
+        if (result == QTN_OK && (ec != cudaSuccess || !graph)) result = QTN_ERR_CUDA;
+    }
+    if (result == QTN_OK && cudaGraphInstantiate(&b->exec, graph, 0) != cudaSuccess) result = QTN_ERR_CUDA;
+    if (graph) cudaGraphDestroy(graph);
+    for (auto e : ev)
+        if (e) cudaEventDestroy(e);
     if (result != QTN_OK) {
-        for (auto e : b->exec) cudaGraphExecDestroy(e);
+        if (b->exec) cudaGraphExecDestroy(b->exec);
         delete b;
         return result;
+    }
+    for (int i = 0; i < count; ++i) {
+        b->stream.push_back(((qtn_context*)ctxs[i])->c.stream);
+        b->sticky.push_back(wss[i].R + R_STICKY);
     }
     b->kernels_per_launch = launch_total() - launches0;
     *batch = b;
@@ -1308,21 +1369,27 @@ qtn_status qtn_batch_create(int count, void* const* ctxs, qtn_mps* items, const 
 qtn_status qtn_batch_launch(void* batch, int repeats) {
     if (!batch || repeats < 0) return QTN_ERR_ARG;
     qtn_batch* b = (qtn_batch*)batch;
-    for (int rep = 0; rep < repeats; ++rep)
-        for (size_t i = 0; i < b->exec.size(); ++i) CK(cudaGraphLaunch(b->exec[i], b->stream[i]));
+    for (int rep = 0; rep < repeats; ++rep) CK(cudaGraphLaunch(b->exec, b->master));
     add_launches(b->kernels_per_launch * repeats);
+    return QTN_OK;
+}
+
+qtn_status qtn_batch_stream(void* batch, void** stream) {
+    if (!batch || !stream) return QTN_ERR_ARG;
+    *stream = (void*)((qtn_batch*)batch)->master;
     return QTN_OK;
 }
 
 qtn_status qtn_batch_sync(void* batch) {
     if (!batch) return QTN_ERR_ARG;
     qtn_batch* b = (qtn_batch*)batch;
+    CK(cudaStreamSynchronize(b->master));
     int worst = 0;
-    for (size_t i = 0; i < b->exec.size(); ++i) {
+    for (size_t i = 0; i < b->sticky.size(); ++i) {
         int f = 0;
-        CK(cudaMemcpyAsync(&f, b->sticky[i], sizeof(int), cudaMemcpyDeviceToHost, b->stream[i]));
-        CK(cudaMemsetAsync(b->sticky[i], 0, sizeof(int), b->stream[i]));
-        CK(cudaStreamSynchronize(b->stream[i]));
+        CK(cudaMemcpyAsync(&f, b->sticky[i], sizeof(int), cudaMemcpyDeviceToHost, b->master));
+        CK(cudaMemsetAsync(b->sticky[i], 0, sizeof(int), b->master));
+        CK(cudaStreamSynchronize(b->master));
         worst |= f;
     }
     return flags_status(worst);
@@ -1331,8 +1398,147 @@ qtn_status qtn_batch_sync(void* batch) {
 qtn_status qtn_batch_destroy(void* batch) {
     if (!batch) return QTN_OK;
     qtn_batch* b = (qtn_batch*)batch;
-    for (auto e : b->exec) cudaGraphExecDestroy(e);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
     delete b;
+    return QTN_OK;
+}
+
+qtn_status qtn_batch_tune_branches(int count, void* const* ctxs, qtn_mps* items, const qtn_mpo* qft,
+                                   const qtn_mpo* qft_dagger, const qtn_mpo* phase, qtn_trunc trunc, void* const* ws,
+                                   const size_t* ws_bytes, const int* candidates, int n_candidates,
+                                   const char* cache_path, int* best_out, double* ms_out) {
+    if (count < 1 || !candidates || n_candidates < 1 || !best_out || !ctxs || !items) return QTN_ERR_ARG;
+    // workload key: device, item count and the (n, chi) multiset of the items
+    qtn_context* x0 = (qtn_context*)ctxs[0];
+    if (!x0) return QTN_ERR_ARG;
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, x0->c.device));
+    unsigned long long h = 1469598103934665603ull;
+    for (int i = 0; i < count; ++i) {
+        h = (h ^ (unsigned long long)items[i].n_sites) * 1099511628211ull;
+        h = (h ^ (unsigned long long)items[i].chi_cap) * 1099511628211ull;
+    }
+    char key[512];
+    snprintf(key, sizeof(key), "batch_branches|%s|count=%d|items=%016llx|prec=%d", prop.name, count, h, trunc.prec);
+    for (char* c = key; *c; ++c)
+        if (*c == ' ') *c = '_';
+    const char* path = cache_path ? cache_path : getenv("QTN_TUNE_CACHE");
+    if (path) {
+        if (FILE* f = fopen(path, "r")) {
+            char k[512];
+            int t = 0;
+            double ms = 0.0;
+            int found = 0;
+            while (fscanf(f, "%511s %d %lf", k, &t, &ms) == 3)
+                if (strcmp(k, key) == 0 && t >= 1) { found = 1; *best_out = t; if (ms_out) *ms_out = ms; }
+            fclose(f);
+            if (found) return QTN_OK;
+        }
+    }
+    // one step per candidate after one step of warm-up (the items are advanced by the trials)
+    double best_ms = 1e300;
+    int best = candidates[0];
+    for (int ci = 0; ci < n_candidates; ++ci) {
+        const int br = std::max(1, std::min(candidates[ci], count));
+        void* b = nullptr;
+        qtn_status st = qtn_batch_create(count, ctxs, items, qft, qft_dagger, phase, 1, trunc, ws, ws_bytes, br, &b);
+        if (st) return st;
+        qtn_batch* bb = (qtn_batch*)b;
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        float ms = 0.f;
+        if ((st = qtn_batch_launch(b, 1)) == QTN_OK) {
+            cudaEventRecord(e0, bb->master);
+            st = qtn_batch_launch(b, 1);
+            cudaEventRecord(e1, bb->master);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&ms, e0, e1);
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        qtn_batch_destroy(b);
+        if (st) return st;
+        if (ms < best_ms) { best_ms = ms; best = br; }
+    }
+    *best_out = best;
+    if (ms_out) *ms_out = best_ms;
+    if (path)
+        if (FILE* f = fopen(path, "a")) {
+            fprintf(f, "%s %d %.6f\n", key, best, best_ms);
+            fclose(f);
+        }
+    return QTN_OK;
+}
+
+qtn_status qtn_set_gemm_tile(void* ctx, int tile) {
+    if (!ctx || (tile != 64 && tile != 32)) return QTN_ERR_ARG;
+    ((qtn_context*)ctx)->c.gemm_tile = tile;
+    return QTN_OK;
+}
+
+qtn_status qtn_tune_gemm_tile(void* ctx, qtn_mps* item, const qtn_mpo* qft, const qtn_mpo* qft_dagger,
+                              const qtn_mpo* phase, qtn_trunc trunc, void* ws, size_t ws_bytes, const char* cache_path,
+                              int* tile_out, double* ms_out) {
+    if (!ctx || !item || !qft || !qft_dagger || !phase || !tile_out || !trunc_ok(trunc)) return QTN_ERR_ARG;
+    if (item->d != 4) return QTN_ERR_SHAPE;
+    qtn_context* x = (qtn_context*)ctx;
+    Ws w;
+    qtn_status st = bind_ws(x, ws, ws_bytes, w);
+    if (st) return st;
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, x->c.device));
+    char key[512];
+    snprintf(key, sizeof(key), "gemm_tile|%s|n=%d|d=%d|chi=%d|w=%d|chi_max=%d|prec=%d", prop.name, item->n_sites,
+             item->d, item->chi_cap, std::max(qft->w_max, phase->w_max), trunc.chi_max, trunc.prec);
+    for (char* c = key; *c; ++c)
+        if (*c == ' ') *c = '_';
+    const char* path = cache_path ? cache_path : getenv("QTN_TUNE_CACHE");
+    if (path) {   // a cached decision: "<key> <tile> <ms of the chosen tile>"
+        if (FILE* f = fopen(path, "r")) {
+            char k[512];
+            int t = 0;
+            double ms = 0.0;
+            int found = 0;
+            while (fscanf(f, "%511s %d %lf", k, &t, &ms) == 3)
+                if (strcmp(k, key) == 0 && (t == 64 || t == 32)) { found = 1; *tile_out = t; if (ms_out) *ms_out = ms; }
+            fclose(f);
+            if (found) { x->c.gemm_tile = *tile_out; return QTN_OK; }
+        }
+    }
+    // time one Fresnel step of the item per tile (one step of warm-up first); the item is advanced by the trials
+    const qtn_mpo* ops[3] = {qft, phase, qft_dagger};
+    double best_ms = 1e300;
+    int best = 64;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int tile : {64, 32}) {
+        x->c.gemm_tile = tile;
+        set_gemm_tile(tile);
+        float ms = 0.f;
+        for (int rep = 0; rep < 3 && st == QTN_OK; ++rep) {
+            if (rep == 1) cudaEventRecord(e0, x->c.stream);
+            for (int o = 0; o < 3 && st == QTN_OK; ++o)
+                for (int ax = 0; ax < 2 && st == QTN_OK; ++ax) st = apply_inner(x, w, ops[o], ax, item, trunc, false);
+        }
+        cudaEventRecord(e1, x->c.stream);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (st) break;
+        if (ms / 2.0 < best_ms) { best_ms = ms / 2.0; best = tile; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    x->c.gemm_tile = best;
+    *tile_out = best;
+    if (ms_out) *ms_out = best_ms;
+    if (path)
+        if (FILE* f = fopen(path, "a")) {
+            fprintf(f, "%s %d %.6f\n", key, best, best_ms);
+            fclose(f);
+        }
     return QTN_OK;
 }
 
@@ -1391,7 +1597,8 @@ constexpr WsLayout noalloc_layout() {
     L.Z = take(std::max(gdim * nc, pc * pc) * c8);
     L.total = off;
     // regions of the zip-up and of the dense transforms: not used by the truncated SVD (bound to null)
-    L.T = L.P = L.carry = L.S64 = L.omega = L.X0 = L.X1 = L.b64 = WS_UNUSED;
+    L.T = L.P = L.carry = L.S64 = L.omega = L.X0 = L.X1 = L.b64 = L.tc = WS_UNUSED;
+    L.tc_bytes = 0;
     return L;
 }
 constexpr WsLayout kNoallocLayout = noalloc_layout();
@@ -1448,7 +1655,8 @@ extern "C" qtn_status qtn_tsvd_noalloc(const void* T, int m, int n, qtn_trunc tr
     NoallocDevice nd;
     qtn_status st = noalloc_device(dev, &nd);
     if (st) return st;
-    Ctx c{(cudaStream_t)stream, nd.sm_count, dev};
+    Ctx c{(cudaStream_t)stream, nd.sm_count, dev, 64};
+    set_gemm_tile(64);
     Ws w = ws_bind(nd.base, L);
     cudaStream_t s = c.stream;
     // The array keeps the previous call's contents.  The ledger and the registers are cleared; every other

@@ -147,7 +147,7 @@ extern double* g_prof_ledger;                              // ledger receiving d
 
 // ------------------------------------------------------------------ workspace layout
 struct WsLayout {
-    size_t ledger, regs, T, P, carry, G64, G32, U, lam, Y, Q, S64, Z, X0, X1, omega, b64, total;
+    size_t ledger, regs, T, P, carry, G64, G32, U, lam, Y, Q, S64, Z, X0, X1, omega, b64, tc, tc_bytes, total;
     int m_cap, n_cap, p_cap, chi, d, w, n_sites;
     long long dense;
 };
@@ -158,6 +158,7 @@ struct Ctx {
     cudaStream_t stream;
     int sm_count;
     int device;
+    int gemm_tile;   // 64 or 32: GEMM tile of this context's launches (batch tuner)
 };
 
 // Pointers into the caller's workspace.
@@ -167,6 +168,7 @@ struct Ws {
     float2 *T, *P, *carry, *G32, *U, *Y, *Q, *Z, *X0, *X1;
     double2 *G64, *S64;
     double* lam;
+    void* tc;   // packed split-BF16 operands of the tensor-core site contraction
     WsLayout L;
 };
 
@@ -193,8 +195,14 @@ cudaError_t launch_build64(int kind, int n, double param, double cutoff, double 
 
 // ------------------------------------------------------------------ launches (defined in the .cu files)
 cudaError_t launch_gemm(const GemmDesc& d, int max_m, int max_n, int max_k, const int* R, cudaStream_t s);
-// Split-BF16 tensor-core complex GEMM (STORE/ACCUM only), FP32 accumulation in TMEM (k_tc.cu).
-cudaError_t launch_gemm_tc(const GemmDesc& d, int max_m, int max_n, int max_k, const int* R, cudaStream_t s);
+// Tile (64 or 32) of the generic GEMM launches made by the calling host thread.
+void set_gemm_tile(int tile);
+int gemm_tile();
+// Split-BF16 tensor-core complex GEMM (STORE/ACCUM only), FP32 accumulation in TMEM (k_tc.cu): operands packed
+// into `pack` (tc_pack_bytes of the capacities), then streamed by bulk copies into the tensor cores.
+size_t tc_pack_bytes(int max_m, int max_n, int max_k);
+cudaError_t launch_gemm_tc(const GemmDesc& d, int max_m, int max_n, int max_k, const int* R, void* pack,
+                           size_t pack_bytes, int sm_count, cudaStream_t s);
 cudaError_t launch_refine_basis(const double2* G, Dim ld, Dim r, float2* V, int ldv, const int* R, cudaStream_t s);
 cudaError_t launch_eig(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, double* lam, const int* R,
                        int r_cap, int max_sweeps, double* ledger, cudaStream_t s, int guard_reg = -1, int guard_val = 0,

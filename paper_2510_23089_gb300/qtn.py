@@ -38,6 +38,7 @@ EXPORTS = (
     "qtn_batch_create", "qtn_batch_launch", "qtn_batch_destroy", "qtn_batch_sync",
     "qtn_workspace_init", "qtn_check", "qtn_build_bessel_mpo", "qtn_build_pauliz_mpo",
     "qtn_reverse_sites", "qtn_psf", "qtn_convolve", "qtn_astf_field", "qtn_transfer_step", "qtn_project_apply",
+    "qtn_batch_stream", "qtn_set_gemm_tile", "qtn_tune_gemm_tile", "qtn_batch_tune_branches",
 )
 
 
@@ -106,7 +107,12 @@ def load_library(path: str = LIB_PATH):
         "qtn_hadamard_zipup": [P, mp, I, mp, tr, st, P, S],
         "qtn_overlap_grad": [P, mp, mp, P, P, S],
         "qtn_batch_create": [I, ctypes.POINTER(P), mp, op, op, op, I, tr, ctypes.POINTER(P), ctypes.POINTER(S),
-                             ctypes.POINTER(P)],
+                             I, ctypes.POINTER(P)],
+        "qtn_batch_stream": [P, ctypes.POINTER(P)],
+        "qtn_batch_tune_branches": [I, ctypes.POINTER(P), mp, op, op, op, tr, ctypes.POINTER(P), ctypes.POINTER(S),
+                                    ctypes.POINTER(I), I, ctypes.c_char_p, ctypes.POINTER(I), ctypes.POINTER(D)],
+        "qtn_set_gemm_tile": [P, I],
+        "qtn_tune_gemm_tile": [P, mp, op, op, op, tr, P, S, ctypes.c_char_p, ctypes.POINTER(I), ctypes.POINTER(D)],
         "qtn_batch_launch": [P, I],
         "qtn_batch_sync": [P],
         "qtn_reverse_sites": [P, mp],
@@ -454,6 +460,19 @@ class Engine:
                                           ctypes.byref(st) if stats else None, *self._ws()), "qtn_transfer_step")
         return _stats(st) if stats else None
 
+    def set_gemm_tile(self, tile: int):
+        _check(self.lib.qtn_set_gemm_tile(self.ctx, int(tile)), "qtn_set_gemm_tile")
+
+    def tune_gemm_tile(self, item: MPS, Q: MPO, Qd: MPO, D: MPO, chi_max: int, cutoff: float, prec: str = "fp32",
+                       cache_path: str | None = None):
+        """(tile, ms per step) chosen by qtn_tune_gemm_tile; `item` is advanced by the trial steps."""
+        t, ms = ctypes.c_int(), ctypes.c_double()
+        _check(self.lib.qtn_tune_gemm_tile(self.ctx, ctypes.byref(item.c), ctypes.byref(Q.c), ctypes.byref(Qd.c),
+                                           ctypes.byref(D.c), self.trunc(chi_max, cutoff, prec), *self._ws(),
+                                           cache_path.encode() if cache_path else None, ctypes.byref(t),
+                                           ctypes.byref(ms)), "qtn_tune_gemm_tile")
+        return t.value, ms.value
+
     def check(self):
         """Raises QtnError for any device-side failure since the last check (qtn_check)."""
         _check(self.lib.qtn_check(self.ctx, *self._ws()), "qtn_check")
@@ -480,12 +499,36 @@ class Engine:
         return out
 
 
-class Batch:
-    """Fresnel steps of many independent interleaved items recorded as one CUDA graph per item
-    (qtn_batch_create) and launched together (qtn_batch_launch): item i runs on engines[i]'s stream with
-    engines[i]'s workspace and operators (Qs[i], Qds[i], Ds[i])."""
+def tune_branches(engines, items, Qs, Qds, Ds, chi_max: int, cutoff: float, prec: str, candidates,
+                  cache_path: str | None = None):
+    """(branches, ms per step) chosen by qtn_batch_tune_branches; the items are advanced by the trial steps."""
+    lib = load_library()
+    n = len(items)
+    ctxs = (ctypes.c_void_p * n)(*[e.ctx.value for e in engines])
+    its = (c_mps * n)(*[it.c for it in items])
+    qa = (c_mpo * n)(*[q.c for q in Qs])
+    qda = (c_mpo * n)(*[q.c for q in Qds])
+    da = (c_mpo * n)(*[q.c for q in Ds])
+    wss = (ctypes.c_void_p * n)(*[e.ws.data_ptr() for e in engines])
+    wsb = (ctypes.c_size_t * n)(*[e.ws_bytes for e in engines])
+    cand = (ctypes.c_int * len(candidates))(*candidates)
+    best, ms = ctypes.c_int(), ctypes.c_double()
+    _check(lib.qtn_batch_tune_branches(n, ctxs, its, qa, qda, da, Engine.trunc(chi_max, cutoff, prec), wss, wsb, cand,
+                                       len(candidates), cache_path.encode() if cache_path else None,
+                                       ctypes.byref(best), ctypes.byref(ms)), "qtn_batch_tune_branches")
+    for it, c in zip(items, its):
+        it.c.canon = c.canon
+    return best.value, ms.value
 
-    def __init__(self, engines, items, Qs, Qds, Ds, n_steps: int, chi_max: int, cutoff: float, prec: str = "fp32"):
+
+class Batch:
+    """Fresnel steps of many independent interleaved items recorded as ONE CUDA graph (qtn_batch_create) of
+    `branches` parallel branches and launched with one call per step (qtn_batch_launch): item i uses
+    engines[i]'s workspace, GEMM tile and operators (Qs[i], Qds[i], Ds[i]); the branches run on the streams of
+    the first `branches` engines."""
+
+    def __init__(self, engines, items, Qs, Qds, Ds, n_steps: int, chi_max: int, cutoff: float, prec: str = "fp32",
+                 branches: int = 0):
         lib = load_library()
         self.lib, self.count = lib, len(items)
         self._keep = (engines, items, Qs, Qds, Ds)
@@ -499,8 +542,9 @@ class Batch:
         wsb = (ctypes.c_size_t * n)(*[e.ws_bytes for e in engines])
         h = ctypes.c_void_p()
         _check(lib.qtn_batch_create(n, ctxs, its, qa, qda, da, n_steps, Engine.trunc(chi_max, cutoff, prec), wss, wsb,
-                                    ctypes.byref(h)), "qtn_batch_create")
+                                    int(branches), ctypes.byref(h)), "qtn_batch_create")
         self.handle = h
+        self.stream = engines[0].stream
 
     def launch(self, repeats: int = 1):
         _check(self.lib.qtn_batch_launch(self.handle, repeats), "qtn_batch_launch")

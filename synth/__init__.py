@@ -21,4 +21,5 @@ from .fields import (  # noqa: F401
     random_mps_sites,
     random_unitary_sites,
     physical_constants,
+    pupil_field,
 )
