@@ -297,9 +297,9 @@ qtn_status qtn_add(void* ctx, const qtn_mps* a, const qtn_mps* b, qtn_mps* out);
  * without running them: the items are split into `branches` parallel branches
  * (<= 0: one per item), assigned longest-first by the cost n chi^3 of a step
  * to the least loaded branch, each branch running its items one after the
- * other on the stream of one of the first `branches` contexts (those streams
- * must be distinct); the branches fork from and join into the first context's
- * stream.  qtn_batch_launch(batch, k) launches that graph k times on that
+ * other; branch 0 runs on the first context's stream, the others on streams
+ * the batch creates (and destroys with it), forked from and joined into the
+ * first context's stream (contexts may share a stream).  qtn_batch_launch(batch, k) launches that graph k times on that
  * stream (qtn_batch_stream returns it), so all items advance concurrently in
  * one launch.  Each item truncates to min(trunc.chi_max, its chi_cap) (its
  * chi_cap when chi_max <= 0) and uses its context's GEMM tile

@@ -134,12 +134,19 @@ __global__ void __launch_bounds__(G_THREADS) k_gemm_t(GemmDesc d, const int* __r
 
 // GEMM tile of the launches made by the calling host thread (set per context by the entry points).
 static thread_local int t_gemm_tile = 64;
+static thread_local int t_gemm_sms = 0;       // SMs of the calling context's device (0: never shrink the tile)
 void set_gemm_tile(int tile) { t_gemm_tile = (tile == 32) ? 32 : 64; }
+void set_gemm_sms(int sms) { t_gemm_sms = sms > 0 ? sms : 0; }
 int gemm_tile() { return t_gemm_tile; }
 
 cudaError_t launch_gemm(const GemmDesc& d, int max_m, int max_n, int max_k, const int* R, cudaStream_t s) {
     if (max_m <= 0 || max_n <= 0) return cudaSuccess;
-    const int T = t_gemm_tile;
+    int T = t_gemm_tile;
+    // a 64-wide tiling that leaves most SMs idle (the skinny products of the range finder and the projections)
+    // takes the 32-wide tile: four times the CTAs
+    if (T == 64 && d.mode != OUT_ATOMIC64 && max_k >= 64 &&
+        (long long)((max_n + 63) / 64) * ((max_m + 63) / 64) * 2 < (long long)t_gemm_sms)
+        T = 32;
     dim3 grid((max_n + T - 1) / T, (max_m + T - 1) / T, 1);
     if (d.mode == OUT_ATOMIC64) {
         int kc = d.kchunk > 0 ? d.kchunk : 1;
@@ -278,99 +285,101 @@ __device__ __forceinline__ void jacobi_pair(float2* __restrict__ W, float* __res
     }
 }
 
-__global__ void __launch_bounds__(EIG_THREADS, 1)
-k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restrict__ U, Dim ldud,
-             double* __restrict__ lam, const int* Rc, int* Rw, int max_sweeps,   // Rc, Rw: one register array
-             double* __restrict__ ledger, int guard_reg, int guard_val, double* __restrict__ prof, float tol,
-             float dead_rel, int report_nonconv) {
-    if (guard_reg >= 0 && Rc[guard_reg] != guard_val) return;
-    extern __shared__ float2 W[];                // column-major, W[j*EIG_RS + i]
+// The cross-block pair (ci, cj) split over the three warps of a block pair: warp `sub` owns the rows
+// [r0, r1) and its 4-lane group (lane li, mask gmask) the rows r0 + li, r0 + li + 4, ...  Each warp adds its
+// partial inner product into part[sub][q], the three warps meet at named barrier bar_id (96 threads), every
+// warp forms the same total (fixed summation order) and the same rotation and rotates its own rows; warp 0
+// keeps the carried norms, slots and flags, and a second barrier ends the step.  The skip test of
+// jacobi_pair reads slots written before the previous step's second barrier, so the three warps always take
+// the same branch.
+__device__ __forceinline__ void bar_named(int id, int count) {
+    __syncwarp();
+    asm volatile("barrier.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void jacobi_pair3(float2* __restrict__ W, float* __restrict__ cn2, int* __restrict__ tmod,
+                                             float2* __restrict__ part, int r, int r16, int col_i, int col_j, int q,
+                                             int li, unsigned gmask, int sub, int r0, int r1, int bar_id, int g,
+                                             int SL, bool first_sweep, float tol, int* rotated, int* sig_rotated,
+                                             unsigned long long& my_pairs, unsigned long long& my_rot) {
+    bool skip = !(col_i < r && col_j < r);
+    int si = 0, sj = 0;
+    if (!skip) {
+        si = jacobi_slot(col_i, r16);
+        sj = jacobi_slot(col_j, r16);
+        if (!first_sweep && max(tmod[si], tmod[sj]) < g - SL) skip = true;
+    }
+    float2* wi = W + si * EIG_RS;
+    float2* wj = W + sj * EIG_RS;
+    float cr = 0.f, ci = 0.f;
+    if (!skip) {
+        float cr1 = 0.f, ci1 = 0.f;
+        int row = r0 + li;
+        for (; row + 4 < r1; row += 8) {
+            const float2 x0 = wi[row], y0 = wj[row], x1 = wi[row + 4], y1 = wj[row + 4];
+            cr = fmaf(x0.x, y0.x, fmaf(x0.y, y0.y, cr));      // conj(x) * y
+            ci = fmaf(x0.x, y0.y, fmaf(-x0.y, y0.x, ci));
+            cr1 = fmaf(x1.x, y1.x, fmaf(x1.y, y1.y, cr1));
+            ci1 = fmaf(x1.x, y1.y, fmaf(-x1.y, y1.x, ci1));
+        }
+        if (row < r1) {
+            const float2 x0 = wi[row], y0 = wj[row];
+            cr = fmaf(x0.x, y0.x, fmaf(x0.y, y0.y, cr));
+            ci = fmaf(x0.x, y0.y, fmaf(-x0.y, y0.x, ci));
+        }
+        cr += cr1;
+        ci += ci1;
+        cr += __shfl_xor_sync(gmask, cr, 2);
+        ci += __shfl_xor_sync(gmask, ci, 2);
+        cr += __shfl_xor_sync(gmask, cr, 1);
+        ci += __shfl_xor_sync(gmask, ci, 1);
+    }
+    if (li == 0) part[sub * EIG_BS + q] = make_float2(cr, ci);
+    bar_named(bar_id, 96);
+    if (!skip) {
+        const float2 p0 = part[q], p1 = part[EIG_BS + q], p2 = part[2 * EIG_BS + q];
+        cr = (p0.x + p1.x) + p2.x;
+        ci = (p0.y + p1.y) + p2.y;
+        const bool lead = (sub == 0 && li == 0);
+        if (lead) ++my_pairs;
+        const float a = cn2[si], b = cn2[sj];
+        const float c2 = fmaf(cr, cr, ci * ci);
+        const float ab2 = a * b;
+        if (c2 > tol * tol * ab2 && c2 > 0.f && ab2 > EIG_NOISE * EIG_NOISE) {
+            const float ic = rsqrtf(c2), cabs = c2 * ic;
+            const float zeta = 0.5f * (b - a) * ic;
+            const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+            const float cs = rsqrtf(fmaf(tt, tt, 1.f));
+            const float tc = tt * cs * ic;
+            const float pr = tc * cr, pi = tc * ci;
+            for (int rw = r0 + li; rw < r1; rw += 4) {
+                const float2 x = wi[rw], y = wj[rw];
+                wi[rw] = make_float2(fmaf(cs, x.x, -fmaf(pr, y.x, pi * y.y)), fmaf(cs, x.y, -fmaf(pr, y.y, -pi * y.x)));
+                wj[rw] = make_float2(fmaf(cs, y.x, fmaf(pr, x.x, -pi * x.y)), fmaf(cs, y.y, fmaf(pr, x.y, pi * x.x)));
+            }
+            if (lead) {
+                cn2[si] = fmaxf(a - tt * cabs, 0.f);
+                cn2[sj] = b + tt * cabs;
+                tmod[si] = g;
+                tmod[sj] = g;
+                *rotated = 1;
+                if (ab2 > EIG_SIG * EIG_SIG) *sig_rotated = 1;
+                ++my_rot;
+            }
+        }
+    }
+    bar_named(bar_id, 96);
+}
+
+// After the sweeps: eigenvalues from the column norms (FP64 accumulation), the columns re-orthonormalised
+// in descending-eigenvalue order and completed, U and lam written (all r x r of W in this CTA's shared memory,
+// column j at W + j * EIG_RS, in the units of the scaled Gram).
+__device__ void eig_finish(float2* __restrict__ W, int r, double gscale, float2* __restrict__ U, long long ldu,
+                           double* __restrict__ lam, float dead_rel) {
     __shared__ double nrm[EIG_MAX];
     __shared__ int rank_of[EIG_MAX];
-    __shared__ int rotated, sig_rotated;
-    const int r = rdim.eval(Rc);
-    const long long ld = ldd.eval(Rc), ldu = ldud.eval(Rc);
-    if (r <= 0) return;
-    __shared__ double gscale, nmax_s;
-    __shared__ unsigned long long n_pairs, n_rot;
+    __shared__ double nmax_s;
     const int tid = threadIdx.x;
-    if (tid == 0) { n_pairs = 0ull; n_rot = 0ull; }
-    // Scale by the largest diagonal entry so that squared column norms stay inside the FP32 range
-    // (one-sided Jacobi on a Gram matrix works with fourth powers of the singular values).
-    if (tid < 32) {
-        double mx = 0.0;
-        for (int i = tid; i < r; i += 32) mx = fmax(mx, fabs(G[(long long)i * ld + i].x));
-        for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-        if (tid == 0) gscale = (mx > 0.0 && isfinite(mx)) ? mx : 1.0;
-    }
-    __syncthreads();
-    const double inv_scale = 1.0 / gscale;
-    for (int e = tid; e < r * r; e += EIG_THREADS) {
-        int i = e / r, j = e % r;                // G row-major; W column j holds G[:, j] / scale
-        double2 g = G[(long long)i * ld + j];
-        W[j * EIG_RS + i] = make_float2((float)(g.x * inv_scale), (float)(g.y * inv_scale));
-    }
-    __syncthreads();
-
-    // squared column norms, exact at the start of every sweep and carried through each rotation by
-    // |x'|^2 = |x|^2 - t |c|, |y'|^2 = |y|^2 + t |c|, so a pair needs only its inner product
-    __shared__ float cn2[EIG_MAX];
-    unsigned long long my_pairs = 0ull, my_rot = 0ull;
-    __shared__ int tmod[EIG_MAX];                // slot of the last rotation of each column (by shared slot)
-    for (int j = tid; j < r; j += EIG_THREADS) tmod[j] = -1;
-    const int nblk = (r + EIG_BS - 1) / EIG_BS, nbr = nblk + (nblk & 1);
-    const int SL = (EIG_BS - 1) + (nbr - 1) * EIG_BS;   // comparison slots per sweep
-    const int r16 = r & ~15;
-    const int warp_j = tid / 32, lane_j = tid % 32;
-    int sweep = 0;
-    bool converged = (r < 2);
-    for (; sweep < max_sweeps && !converged; ++sweep) {
-        if (tid == 0) { rotated = 0; sig_rotated = 0; }
-        for (int j = tid / 32; j < r; j += EIG_THREADS / 32) {
-            float s2 = 0.f;
-            for (int row = tid % 32; row < r; row += 32) {
-                const float2 x = W[j * EIG_RS + row];
-                s2 = fmaf(x.x, x.x, fmaf(x.y, x.y, s2));
-            }
-            for (int off = 16; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
-            if (tid % 32 == 0) cn2[j] = s2;
-        }
-        __syncthreads();
-        const int g0 = sweep * SL;
-        if (warp_j < nblk) {                     // pairs inside block warp_j
-            const int k = lane_j >> 3, li = lane_j & 7;
-            const unsigned gmask = 0xFFu << (8 * k);
-            for (int u = 0; u < EIG_BS - 1; ++u) {
-                int a, b;
-                circle_pair(u, k, EIG_BS, a, b);
-                jacobi_pair<8>(W, cn2, tmod, r, r16, warp_j * EIG_BS + a, warp_j * EIG_BS + b, li, gmask, g0 + u, SL,
-                               sweep == 0, tol, &rotated, &sig_rotated, my_pairs, my_rot);
-                __syncwarp();
-            }
-        }
-        __syncthreads();
-        for (int t = 0; t < nbr - 1; ++t) {      // pairs across the blocks of every block pair of round t
-            if (warp_j < nbr / 2) {
-                int A, B;
-                circle_pair(t, warp_j, nbr, A, B);
-                const int q = lane_j >> 2, li = lane_j & 3;
-                const unsigned gmask = 0xFu << (4 * q);
-                for (int s2 = 0; s2 < EIG_BS; ++s2) {
-                    jacobi_pair<4>(W, cn2, tmod, r, r16, A * EIG_BS + q, B * EIG_BS + ((q + s2) & (EIG_BS - 1)), li,
-                                   gmask, g0 + (EIG_BS - 1) + t * EIG_BS + s2, SL, sweep == 0, tol, &rotated, &sig_rotated,
-                                   my_pairs, my_rot);
-                    __syncwarp();
-                }
-            }
-            __syncthreads();
-        }
-        converged = (rotated == 0);
-        __syncthreads();
-    }
-    if (prof != nullptr && (my_pairs | my_rot)) {
-        atomicAdd(&n_pairs, my_pairs);
-        atomicAdd(&n_rot, my_rot);
-    }
     // eigenvalues = column norms (FP64 accumulation), eigenvectors = normalised columns
     for (int j = tid / 32; j < r; j += EIG_THREADS / 32) {
         double s = 0.0;
@@ -667,6 +676,102 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
         int j = e / r, row = e % r;
         U[(long long)rank_of[j] * ldu + row] = W[j * EIG_RS + row];
     }
+}
+
+__global__ void __launch_bounds__(EIG_THREADS, 1)
+k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restrict__ U, Dim ldud,
+             double* __restrict__ lam, const int* Rc, int* Rw, int max_sweeps,   // Rc, Rw: one register array
+             double* __restrict__ ledger, int guard_reg, int guard_val, double* __restrict__ prof, float tol,
+             float dead_rel, int report_nonconv) {
+    if (guard_reg >= 0 && Rc[guard_reg] != guard_val) return;
+    extern __shared__ float2 W[];                // column-major, W[j*EIG_RS + i]
+    __shared__ int rotated, sig_rotated;
+    const int r = rdim.eval(Rc);
+    const long long ld = ldd.eval(Rc), ldu = ldud.eval(Rc);
+    if (r <= 0) return;
+    __shared__ double gscale;
+    __shared__ unsigned long long n_pairs, n_rot;
+    const int tid = threadIdx.x;
+    if (tid == 0) { n_pairs = 0ull; n_rot = 0ull; }
+    // Scale by the largest diagonal entry so that squared column norms stay inside the FP32 range
+    // (one-sided Jacobi on a Gram matrix works with fourth powers of the singular values).
+    if (tid < 32) {
+        double mx = 0.0;
+        for (int i = tid; i < r; i += 32) mx = fmax(mx, fabs(G[(long long)i * ld + i].x));
+        for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        if (tid == 0) gscale = (mx > 0.0 && isfinite(mx)) ? mx : 1.0;
+    }
+    __syncthreads();
+    const double inv_scale = 1.0 / gscale;
+    for (int e = tid; e < r * r; e += EIG_THREADS) {
+        int i = e / r, j = e % r;                // G row-major; W column j holds G[:, j] / scale
+        double2 g = G[(long long)i * ld + j];
+        W[j * EIG_RS + i] = make_float2((float)(g.x * inv_scale), (float)(g.y * inv_scale));
+    }
+    __syncthreads();
+
+    // squared column norms, exact at the start of every sweep and carried through each rotation by
+    // |x'|^2 = |x|^2 - t |c|, |y'|^2 = |y|^2 + t |c|, so a pair needs only its inner product
+    __shared__ float cn2[EIG_MAX];
+    unsigned long long my_pairs = 0ull, my_rot = 0ull;
+    __shared__ int tmod[EIG_MAX];                // slot of the last rotation of each column (by shared slot)
+    __shared__ float2 part[(EIG_MAX / EIG_BS / 2) * 3 * EIG_BS];   // partial inner products per block pair
+    for (int j = tid; j < r; j += EIG_THREADS) tmod[j] = -1;
+    const int nblk = (r + EIG_BS - 1) / EIG_BS, nbr = nblk + (nblk & 1);
+    const int SL = (EIG_BS - 1) + (nbr - 1) * EIG_BS;   // comparison slots per sweep
+    const int r16 = r & ~15;
+    const int warp_j = tid / 32, lane_j = tid % 32;
+    int sweep = 0;
+    bool converged = (r < 2);
+    for (; sweep < max_sweeps && !converged; ++sweep) {
+        if (tid == 0) { rotated = 0; sig_rotated = 0; }
+        for (int j = tid / 32; j < r; j += EIG_THREADS / 32) {
+            float s2 = 0.f;
+            for (int row = tid % 32; row < r; row += 32) {
+                const float2 x = W[j * EIG_RS + row];
+                s2 = fmaf(x.x, x.x, fmaf(x.y, x.y, s2));
+            }
+            for (int off = 16; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+            if (tid % 32 == 0) cn2[j] = s2;
+        }
+        __syncthreads();
+        const int g0 = sweep * SL;
+        if (warp_j < nblk) {                     // pairs inside block warp_j
+            const int k = lane_j >> 3, li = lane_j & 7;
+            const unsigned gmask = 0xFFu << (8 * k);
+            for (int u = 0; u < EIG_BS - 1; ++u) {
+                int a, b;
+                circle_pair(u, k, EIG_BS, a, b);
+                jacobi_pair<8>(W, cn2, tmod, r, r16, warp_j * EIG_BS + a, warp_j * EIG_BS + b, li, gmask, g0 + u, SL,
+                               sweep == 0, tol, &rotated, &sig_rotated, my_pairs, my_rot);
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        for (int t = 0; t < nbr - 1; ++t) {      // pairs across the blocks of every block pair of round t
+            const int bp = warp_j / 3, sub = warp_j % 3;   // three warps per block pair, a third of the rows each
+            if (bp < nbr / 2) {
+                int A, B;
+                circle_pair(t, bp, nbr, A, B);
+                const int q = lane_j >> 2, li = lane_j & 3;
+                const unsigned gmask = 0xFu << (4 * q);
+                const int rt = (r + 2) / 3, r0 = min(r, sub * rt), r1 = min(r, r0 + rt);
+                for (int s2 = 0; s2 < EIG_BS; ++s2)
+                    jacobi_pair3(W, cn2, tmod, part + bp * 3 * EIG_BS, r, r16, A * EIG_BS + q,
+                                 B * EIG_BS + ((q + s2) & (EIG_BS - 1)), q, li, gmask, sub, r0, r1, 1 + bp,
+                                 g0 + (EIG_BS - 1) + t * EIG_BS + s2, SL, sweep == 0, tol, &rotated, &sig_rotated,
+                                 my_pairs, my_rot);
+            }
+            __syncthreads();
+        }
+        converged = (rotated == 0);
+        __syncthreads();
+    }
+    if (prof != nullptr && (my_pairs | my_rot)) {
+        atomicAdd(&n_pairs, my_pairs);
+        atomicAdd(&n_rot, my_rot);
+    }
+    eig_finish(W, r, gscale, U, ldu, lam, dead_rel);
     if (tid == 0) {
         atomicMax(&Rw[R_SWEEPS], sweep);
         // unconverged only when the last sweep still rotated a pair above the rounding level of the scaled Gram
@@ -681,12 +786,12 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
 cudaError_t launch_eig(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, double* lam, const int* R,
                        int r_cap, int max_sweeps, double* ledger, cudaStream_t s, int guard_reg, int guard_val,
                        float tol, float dead_rel, bool report_nonconv) {
-    (void)r_cap;
     const size_t smem = (size_t)EIG_MAX * EIG_RS * sizeof(float2);
     count_launch(PROF_EIG, s, true);
+    double* prof = g_prof_ledger ? g_prof_ledger + L_PROF_EIG : nullptr;
+    (void)r_cap;
     k_eig_jacobi<<<1, EIG_THREADS, smem, s>>>(G, ld, r, U, ldu, lam, R, (int*)R, max_sweeps, ledger, guard_reg,
-                                               guard_val, g_prof_ledger ? g_prof_ledger + L_PROF_EIG : nullptr, tol,
-                                               dead_rel, report_nonconv ? 1 : 0);
+                                               guard_val, prof, tol, dead_rel, report_nonconv ? 1 : 0);
     count_launch(PROF_EIG, s, false);
     return cudaGetLastError();
 }
@@ -716,6 +821,9 @@ static void prof_drain(ProfPool& p) {
 void count_launch(int cls, cudaStream_t s, bool before) {
     if (!before) g_launches.fetch_add(1, std::memory_order_relaxed);
     if (!g_prof_on || cls == PROF_OTHER) return;
+    // launches recorded into a graph are not timed here (an event node cannot sit in a conditional body)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
     ProfPool& p = g_pool[cls];
     if (before) {
         if (p.used + 2 > p.cap) prof_drain(p);   // every launch is timed: a full pool is drained, not skipped

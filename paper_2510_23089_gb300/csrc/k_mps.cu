@@ -297,6 +297,60 @@ __global__ void __launch_bounds__(1024) k_cgs_block_8(float2* Q, int ld, Dim mdi
     cgs_block_body<8, 2048>(Q, ld, mdim, c0, ncols, pre, R, greg, decide);
 }
 
+// Range finder with a rank-deficient sketch (R_DEP = 1): the block Gram-Schmidt left the dependent columns of
+// the m x ld basis exactly zero.  k_sketch_live finds the live columns (one CTA), keeps their order, and makes
+// their count the subspace size of everything that follows (R_P, and R_ROWS for the refinement); k_sketch_gather
+// moves them to the front (reading a copy), so the Rayleigh-Ritz problem shrinks from EIG_MAX to the rank.
+__global__ void k_sketch_live(const float2* __restrict__ Y, int ld, Dim mdim, int pc, int* __restrict__ perm,
+                              int* __restrict__ R) {
+    if (!(R[R_RAND] == 1 && R[R_DEP] == 1)) return;
+    const int m = mdim.eval(R);
+    __shared__ int live[1024];
+    for (int c = threadIdx.x; c < pc; c += blockDim.x) {
+        int nz = 0;
+        for (int row = 0; row < m && !nz; ++row) {
+            const float2 v = Y[(long long)row * ld + c];
+            nz = (v.x != 0.f || v.y != 0.f);
+        }
+        live[c] = nz;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int k = 0;
+        for (int c = 0; c < pc; ++c)
+            if (live[c]) perm[k++] = c;
+        const int nl = max(k, 1);
+        for (int c = 0; c < pc; ++c)
+            if (!live[c] && k < pc) perm[k++] = c;
+        R[R_P] = nl;
+        R[R_ROWS] = nl;
+    }
+}
+
+__global__ void k_sketch_gather(const float2* __restrict__ src, float2* __restrict__ Y, int ld, Dim mdim, int pc,
+                                const int* __restrict__ perm, const int* __restrict__ R) {
+    if (!(R[R_RAND] == 1 && R[R_DEP] == 1)) return;
+    const int m = mdim.eval(R);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)m * pc;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int row = (int)(e / pc), j = (int)(e % pc);
+        Y[(long long)row * ld + j] = src[(long long)row * ld + perm[j]];
+    }
+}
+
+// Newton-Schulz coefficient matrix E = (3 I - S) / 2 of an FP64 Gram S = U^dagger U (r x r, row-major),
+// rounded to FP32 (entries near 1 on the diagonal, near 0 off it).
+__global__ void k_ns_coeff(const double2* __restrict__ S, int lds, float2* __restrict__ E, int lde, Dim rdim,
+                           const int* __restrict__ R) {
+    const int r = rdim.eval(R);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)r * r;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / r), j = (int)(e % r);
+        const double2 v = S[(long long)i * lds + j];
+        E[(long long)i * lde + j] = make_float2((float)((i == j ? 1.5 : 0.0) - 0.5 * v.x), (float)(-0.5 * v.y));
+    }
+}
+
 // Guarded copy of n elements (runs when R[greg] == gval).
 __global__ void k_copy_guarded(const float2* __restrict__ src, float2* __restrict__ dst, long long n,
                                const int* __restrict__ R, int greg, int gval) {

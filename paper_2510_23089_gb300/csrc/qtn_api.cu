@@ -9,8 +9,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cmath>
+#include <functional>
 #include <mutex>
 #include <vector>
 
@@ -27,11 +29,14 @@ __global__ void k_trace(const double2*, int, Dim, int*, double*);
 __global__ void k_path(Dim, int*, double*);
 __global__ void k_total_weight(const float2*, Dim, Dim, Dim, const int*, double*);
 __global__ void k_cgs_block_32(float2*, int, Dim, int, int, const float*, int*, int, int);
+__global__ void k_ns_coeff(const double2*, int, float2*, int, Dim, const int*);
 __global__ void k_cgs_block_16(float2*, int, Dim, int, int, const float*, int*, int, int);
 __global__ void k_cgs_block_8(float2*, int, Dim, int, int, const float*, int*, int, int);
 __global__ void k_col_norms(const float2*, int, Dim, Dim, float*, const int*, int);
 __global__ void k_set_pi(int*);
 __global__ void k_copy_guarded(const float2*, float2*, long long, const int*, int, int);
+__global__ void k_sketch_live(const float2*, int, Dim, int, int*, int*);
+__global__ void k_sketch_gather(const float2*, float2*, int, Dim, int, const int*, const int*);
 __global__ void k_kron_interleave(const float2*, const int*, int, const float2*, const int*, int, float2*, int*, int,
                                   int);
 __global__ void k_direct_sum(const float2*, const int*, int, const float2*, const int*, int, float2*, int*, int, int,
@@ -228,6 +233,70 @@ struct TsvdIO {
     float2* X;           // output rows U^dagger T, row stride R_N, capacity m_cap x n_cap (or p x n)
 };
 
+// Kernels launched inside the bodies of conditional graph nodes that ran (added by the condition kernel, so
+// that the launch count reports what executed, not what was recorded).
+__device__ unsigned long long g_cond_launches = 0;
+static std::atomic<bool> g_cond_used{false};
+
+// Condition of a graph conditional node from a dimension register: R[reg] == val selects the first body.
+__global__ void k_set_cond(cudaGraphConditionalHandle h, const int* __restrict__ R, int reg, int val,
+                           unsigned long long n_first, unsigned long long n_second) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const bool first = (R[reg] == val);
+        cudaGraphSetConditional(h, first ? 1u : 0u);
+        atomicAdd(&g_cond_launches, first ? n_first : n_second);
+    }
+}
+
+// Under stream capture on `s`: records a conditional node whose first body (then_fn) runs when R[reg] == val
+// and whose second body (else_fn, when given) runs otherwise.  The bodies are captured into the node's child
+// graphs on the context's helper stream of nesting level `depth` (the enqueueing code reads its stream from
+// `s`, which is switched for the duration); the condition kernel follows on `s` and the node depends on it;
+// capture of the outer graph continues after the node.
+static qtn_status capture_if(Ctx* c, cudaStream_t& s, int* R, int reg, int val, int depth,
+                             const std::function<qtn_status()>& then_fn, const std::function<qtn_status()>& else_fn) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.size = else_fn ? 2 : 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p));
+    const cudaStream_t outer = s;
+    const cudaStream_t helper = c->helper[depth];
+    long long n_body[2] = {0, 0};
+    for (unsigned b = 0; b < p.conditional.size; ++b) {
+        CK(cudaStreamBeginCaptureToGraph(helper, p.conditional.phGraph_out[b], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeRelaxed));
+        const long long l0 = launch_total();
+        s = helper;
+        const qtn_status st = (b == 0) ? then_fn() : else_fn();
+        s = outer;
+        n_body[b] = launch_total() - l0;
+        cudaGraph_t body = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(helper, &body);
+        if (st) return st;
+        CK(e);
+    }
+    add_launches(-(n_body[0] + n_body[1]));   // counted on the device by the condition kernel instead
+    g_cond_used = true;
+    k_set_cond<<<1, 1, 0, s>>>(h, R, reg, val, (unsigned long long)n_body[0], (unsigned long long)n_body[1]);
+    CKL();
+    count_launch(PROF_OTHER, s, false);
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+    std::vector<cudaGraphNode_t> to(nd, node);
+    CK(cudaGraphAddDependencies(g, deps, to.data(), nullptr, nd));
+    CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return QTN_OK;
+}
+
 static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int chi_cap_out, Dim& rows_out) {
     cudaStream_t s = c->stream;
     const int mc = io.m_cap;
@@ -251,6 +320,9 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
     constexpr float TOL_REFINE = 3e-6f;
     k_path<<<1, 1, 0, s>>>(io.m, w.R, w.ledger);
     CKL();
+    cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s, &cap_status));
+    const bool capturing = (cap_status == cudaStreamCaptureStatusActive) && c->helper[1] != nullptr;
     // Gram G = A A^dagger of an m x n matrix with row stride ld (FP32 products, FP64 split-K accumulation)
     auto gram = [&](const float2* A, Dim m, Dim ld, Dim n, int m_cap, int guard, bool zero,
                     long long n_cap) -> qtn_status {
@@ -271,6 +343,7 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
     };
     qtn_status st;
     // ---- shared-memory path (m <= EIG_MAX): eigenbasis U of G = T T^dagger, X = U^dagger T
+    auto shared_path = [&]() -> qtn_status {
     if ((st = gram(io.T, io.m, io.n, io.n, std::min(mc, EIG_MAX), 0, true, io.n_cap))) return st;
     k_trace<<<1, 256, 0, s>>>(w.G64, gld, io.m, w.R, w.ledger);
     CKL();
@@ -285,9 +358,11 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
         g.guard_reg = R_RAND; g.guard_val = 0;
         CK(launch_gemm(g, std::min(mc, EIG_MAX), ncap, std::min(mc, EIG_MAX), w.R, s));
     }
+    return QTN_OK;
+    };
     // ---- range-finder path (m > EIG_MAX): Q = orth(T Omega) by block CGS2, exact path on B = Q^dagger T,
     //      U = Q U_B.  No product with G is ever formed, so the FP32 dynamic range is that of T itself.
-    if (mc > EIG_MAX) {
+    auto range_path = [&]() -> qtn_status {
         if (mc > CGS_MAXM_ALL) return QTN_ERR_WORKSPACE;
         const int Ph = EIG_MAX;                             // = R[R_P] on this path
         const Dim P = dc(Ph);
@@ -355,6 +430,7 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
         // Three power iterations: for a chi-limited truncation of a slowly decaying spectrum every iteration
         // shrinks the weight the sketch misses near the kept rank by about (s_(p+1) / s_k)^4 (one was measured
         // 2.6e-5 of |T|^2 above the Eckart-Young optimum at 512 x 768, chi 128, s_k / s_1 = 0.08).
+        auto power_iters = [&]() -> qtn_status {
         for (int it = 0; it < RF_POWER_ITERS; ++it) {
             if (one_chunk && ncap <= 2048) {   // Z fits the B buffer whole and the block orthonormaliser
                 {   // Z = T^dagger Q (n x p) in the B buffer
@@ -406,6 +482,28 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
                 CKL();
             }
         }
+        return QTN_OK;
+        };
+        // under graph capture the iterations sit in the body of a conditional node (skipped, not replayed as
+        // no-ops, when the sketch is rank-deficient); eagerly they are launched and retire on the device guard
+        if (capturing) {
+            if ((st = capture_if(c, s, w.R, R_PI, 1, 1, power_iters, nullptr))) return st;
+        } else if ((st = power_iters())) {
+            return st;
+        }
+        // a rank-deficient sketch: its live columns first, their count the subspace size from here on
+        {
+            int* sperm = (int*)ws_lam2(w);
+            k_sketch_live<<<1, 256, 0, s>>>(w.Y, pc, io.m, pc, sperm, w.R);
+            CKL();
+            k_copy_guarded<<<grid_for((long long)mc * pc, 256, c->sm_count), 256, 0, s>>>(w.Y, w.Q, (long long)mc * pc,
+                                                                                       w.R, R_DEP, 1);
+            CKL();
+            k_sketch_gather<<<grid_for((long long)mc * pc, 256, c->sm_count), 256, 0, s>>>(w.Q, w.Y, pc, io.m, pc,
+                                                                                        sperm, w.R);
+            CKL();
+        }
+        const Dim Pl = dr(R_P);    // live subspace size (EIG_MAX for a full-rank sketch)
         float2* Qb = w.Y;          // orthonormal basis of the sketch
         float2* UB = w.Q;          // eigenvectors of the Gram of B (p x p, column-major)
         // Gram of B = Q^dagger T accumulated over column chunks of T that fit the B buffer (B is never
@@ -418,19 +516,19 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
             g.A = mat(Qb, dc(1), dc(pc), 1);
             g.B = mat(io.T + c0, io.n, dc(1));
             g.C = w.G32; g.crs = ncol; g.ccs = dc(1);
-            g.M = P; g.N = ncol; g.K = io.m;
+            g.M = Pl; g.N = ncol; g.K = io.m;
             g.guard_reg = R_RAND; g.guard_val = 1;
             CK(launch_gemm(g, pc, cwid, mc, w.R, s));
-            if ((st = gram(w.G32, P, ncol, ncol, pc, 1, false, cwid))) return st;
+            if ((st = gram(w.G32, Pl, ncol, ncol, pc, 1, false, cwid))) return st;
         }
-        CK(launch_eig(w.G64, dc(gld), P, UB, dc(pc), w.lam, w.R, pc, sweeps1, w.ledger, s, R_RAND, 1, tol1, dead1,
+        CK(launch_eig(w.G64, dc(gld), Pl, UB, dc(pc), w.lam, w.R, pc, sweeps1, w.ledger, s, R_RAND, 1, tol1, dead1,
                       false));
         {   // U = Q U_B  (m x p, column-major with leading dimension gld)
             GemmDesc g{};
             g.A = mat(Qb, dc(pc), dc(1));
             g.B = mat(UB, dc(1), dc(pc));
             g.C = w.U; g.crs = dc(1); g.ccs = dc(gld);
-            g.M = io.m; g.N = P; g.K = P;
+            g.M = io.m; g.N = Pl; g.K = Pl;
             g.guard_reg = R_RAND; g.guard_val = 1;
             CK(launch_gemm(g, mc, pc, pc, w.R, s));
         }
@@ -439,10 +537,21 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
             g.A = mat(w.U, dc(gld), dc(1), 1);
             g.B = mat(io.T, io.n, dc(1));
             g.C = io.X; g.crs = io.n; g.ccs = dc(1);
-            g.M = P; g.N = io.n; g.K = io.m;
+            g.M = Pl; g.N = io.n; g.K = io.m;
             g.guard_reg = R_RAND; g.guard_val = 1;
             CK(launch_gemm(g, pc, ncap, mc, w.R, s));
         }
+        return QTN_OK;
+    };
+    // The two paths: under graph capture the bodies of one IF/ELSE conditional node on R_RAND (only the path
+    // taken runs); eagerly both are launched and the one not taken retires on its device guard.
+    if (mc <= EIG_MAX) {
+        if ((st = shared_path())) return st;
+    } else if (capturing) {
+        if ((st = capture_if(c, s, w.R, R_RAND, 1, 0, range_path, shared_path))) return st;
+    } else {
+        if ((st = shared_path())) return st;
+        if ((st = range_path())) return st;
     }
     const Dim rows = dr(R_ROWS);
     const int rcap = std::min(mc, EIG_MAX);
@@ -460,13 +569,38 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
         g.C = w.Q; g.crs = dc(1); g.ccs = dc(gld);
         g.M = io.m; g.N = rows; g.K = rows;
         CK(launch_gemm(g, mc, rcap, rcap, w.R, s));
-        GemmDesc h{};                                   // X = U2^dagger T
-        h.A = mat(w.Q, dc(gld), dc(1), 1);
+        // One Newton-Schulz step U = U2 (3 I - S) / 2 with S = U2^dagger U2 (FP64-accumulated): the eigenbases
+        // are products of FP32 plane rotations, unitary to ~1e-6; the step takes the isometry error to its
+        // square (below the FP32 rounding of the product) without touching the subspace at first order.
+        CK(cudaMemsetAsync(w.G64, 0, (size_t)rcap * gld * sizeof(double2), s));
+        GemmDesc sg{};                                  // S = U2^dagger U2  (rows x rows, FP64)
+        sg.A = mat(w.Q, dc(gld), dc(1), 1);
+        sg.B = mat(w.Q, dc(1), dc(gld));
+        sg.C = w.G64; sg.crs = dc(gld); sg.ccs = dc(1);
+        sg.M = rows; sg.N = rows; sg.K = io.m;
+        sg.mode = OUT_ATOMIC64;
+        {
+            const int tiles = ((rcap + 63) / 64) * ((rcap + 63) / 64);
+            const int want = std::max(1, (c->sm_count * 4) / std::max(tiles, 1));
+            const int kc = std::max(256, (mc + want - 1) / want);
+            sg.kchunk = (kc + 15) / 16 * 16;
+        }
+        CK(launch_gemm(sg, rcap, rcap, mc, w.R, s));
+        k_ns_coeff<<<grid_for((long long)rcap * rcap, 256, c->sm_count), 256, 0, s>>>(w.G64, gld, w.G32, gld, rows,
+                                                                                     w.R);
+        CKL();
+        GemmDesc ng{};                                  // U = U2 (3 I - S) / 2  (column-major, ld gld)
+        ng.A = mat(w.Q, dc(1), dc(gld));
+        ng.B = mat(w.G32, dc(gld), dc(1));
+        ng.C = w.U; ng.crs = dc(1); ng.ccs = dc(gld);
+        ng.M = io.m; ng.N = rows; ng.K = rows;
+        CK(launch_gemm(ng, mc, rcap, rcap, w.R, s));
+        GemmDesc h{};                                   // X = U^dagger T
+        h.A = mat(w.U, dc(gld), dc(1), 1);
         h.B = mat(io.T, io.n, dc(1));
         h.C = io.X; h.crs = io.n; h.ccs = dc(1);
         h.M = rows; h.N = io.n; h.K = io.m;
         CK(launch_gemm(h, rcap, ncap, mc, w.R, s));
-        CK(cudaMemcpyAsync(w.U, w.Q, (size_t)gld * rcap * sizeof(float2), cudaMemcpyDeviceToDevice, s));
     }
     k_row_weights<<<grid_for((long long)gld * 32, 256, c->sm_count), 256, 0, s>>>(io.X, io.n, rows, io.n,
                                                                                     ws_weights(w), w.R);
@@ -595,6 +729,7 @@ using namespace qtn;
 
 qtn_status bind_ws(qtn_context* x, void* ws, size_t bytes, Ws& w) {
     set_gemm_tile(x->c.gemm_tile);
+    set_gemm_sms(x->c.sm_count);
     if (!x->have_layout) return QTN_ERR_WORKSPACE;
     qtn_status st = check_ws(x->L, ws, bytes);
     if (st) return st;
@@ -606,7 +741,11 @@ extern "C" {
 
 int qtn_version(void) { return 1; }
 
-long long qtn_launch_count(void) { return launch_total(); }
+long long qtn_launch_count(void) {
+    unsigned long long cond = 0;
+    if (g_cond_used && cudaMemcpyFromSymbol(&cond, g_cond_launches, sizeof(cond)) != cudaSuccess) cond = 0;
+    return launch_total() + (long long)cond;
+}
 
 qtn_status qtn_profile(void* ctx, int enable, void* ws, size_t ws_bytes) {
     if (!ctx) return QTN_ERR_ARG;
@@ -669,11 +808,18 @@ qtn_status qtn_create(void** ctx, void* stream) {
         return QTN_ERR_CUDA;
     }
     x->c.gemm_tile = 64;
+    // helper streams that capture the bodies of conditional graph nodes (two nesting levels)
+    for (int i = 0; i < 2; ++i)
+        if (cudaStreamCreateWithFlags(&x->c.helper[i], cudaStreamNonBlocking) != cudaSuccess) x->c.helper[i] = nullptr;
     *ctx = x;
     return QTN_OK;
 }
 
 qtn_status qtn_destroy(void* ctx) {
+    if (!ctx) return QTN_OK;
+    qtn_context* x = (qtn_context*)ctx;
+    for (int i = 0; i < 2; ++i)
+        if (x->c.helper[i]) cudaStreamDestroy(x->c.helper[i]);
     free(ctx);
     return QTN_OK;
 }
@@ -1256,6 +1402,7 @@ struct qtn_batch {
     cudaStream_t master = nullptr;
     std::vector<cudaStream_t> stream;   // every item's stream (its status word is read on it)
     std::vector<int*> sticky;           // each item's sticky status word (in its workspace)
+    std::vector<cudaStream_t> own;      // the streams of branches 1.. (created and destroyed by the batch)
     int branches = 1;
     long long kernels_per_launch = 0;
 };
@@ -1280,13 +1427,9 @@ qtn_status qtn_batch_create(int count, void* const* ctxs, qtn_mps* items, const 
         // after a whole number of steps (an item with none would replay its canonicalisation sweep each time)
         if (items[i].canon == QTN_CANON_NONE) return QTN_ERR_ARG;
     }
-    // the branches run on the streams of the first `branches` items; they must be distinct
-    std::vector<cudaStream_t> bs(branches);
-    for (int g = 0; g < branches; ++g) {
-        bs[g] = ((qtn_context*)ctxs[g])->c.stream;
-        for (int h = 0; h < g; ++h)
-            if (bs[h] == bs[g]) return QTN_ERR_ARG;
-    }
+    // branch 0 runs on the first context's stream (the launch stream); the others on streams the batch owns
+    std::vector<cudaStream_t> bs(branches, nullptr);
+    bs[0] = ((qtn_context*)ctxs[0])->c.stream;
     // longest-processing-time assignment of items to branches by the cost of a step ~ n chi^3 (zip-up of chi-wide
     // bonds over n sites)
     std::vector<int> order(count);
@@ -1303,6 +1446,14 @@ qtn_status qtn_batch_create(int count, void* const* ctxs, qtn_mps* items, const 
     qtn_batch* b = new qtn_batch;
     b->master = bs[0];
     b->branches = branches;
+    for (int g = 1; g < branches; ++g) {
+        if (cudaStreamCreateWithFlags(&bs[g], cudaStreamNonBlocking) != cudaSuccess) {
+            bs[g] = nullptr;
+            qtn_batch_destroy(b);
+            return QTN_ERR_CUDA;
+        }
+        b->own.push_back(bs[g]);
+    }
     const long long launches0 = launch_total();
     qtn_status result = QTN_OK;
     std::vector<cudaEvent_t> ev(branches + 1, nullptr);
@@ -1321,6 +1472,7 @@ qtn_status qtn_batch_create(int count, void* const* ctxs, qtn_mps* items, const 
                 const cudaStream_t own = x->c.stream;
                 x->c.stream = bs[g];
                 set_gemm_tile(x->c.gemm_tile);
+                set_gemm_sms(x->c.sm_count);
                 Ws& w = wss[i];
                 qtn_mps* psi = items + i;
                 const int canon0 = psi->canon;
@@ -1353,8 +1505,7 @@ qtn_status qtn_batch_create(int count, void* const* ctxs, qtn_mps* items, const 
     for (auto e : ev)
         if (e) cudaEventDestroy(e);
     if (result != QTN_OK) {
-        if (b->exec) cudaGraphExecDestroy(b->exec);
-        delete b;
+        qtn_batch_destroy(b);
         return result;
     }
     for (int i = 0; i < count; ++i) {
@@ -1399,6 +1550,7 @@ qtn_status qtn_batch_destroy(void* batch) {
     if (!batch) return QTN_OK;
     qtn_batch* b = (qtn_batch*)batch;
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (cudaStream_t t : b->own) cudaStreamDestroy(t);
     delete b;
     return QTN_OK;
 }
@@ -1655,8 +1807,9 @@ extern "C" qtn_status qtn_tsvd_noalloc(const void* T, int m, int n, qtn_trunc tr
     NoallocDevice nd;
     qtn_status st = noalloc_device(dev, &nd);
     if (st) return st;
-    Ctx c{(cudaStream_t)stream, nd.sm_count, dev, 64};
+    Ctx c{(cudaStream_t)stream, nd.sm_count, dev, 64, {nullptr, nullptr}};
     set_gemm_tile(64);
+    set_gemm_sms(nd.sm_count);
     Ws w = ws_bind(nd.base, L);
     cudaStream_t s = c.stream;
     // The array keeps the previous call's contents.  The ledger and the registers are cleared; every other

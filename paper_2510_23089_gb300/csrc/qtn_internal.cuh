@@ -159,6 +159,7 @@ struct Ctx {
     int sm_count;
     int device;
     int gemm_tile;   // 64 or 32: GEMM tile of this context's launches (batch tuner)
+    cudaStream_t helper[2];   // capture the bodies of conditional graph nodes (null: guards only)
 };
 
 // Pointers into the caller's workspace.
@@ -197,6 +198,7 @@ cudaError_t launch_build64(int kind, int n, double param, double cutoff, double 
 cudaError_t launch_gemm(const GemmDesc& d, int max_m, int max_n, int max_k, const int* R, cudaStream_t s);
 // Tile (64 or 32) of the generic GEMM launches made by the calling host thread.
 void set_gemm_tile(int tile);
+void set_gemm_sms(int sms);   // SM count of the calling context's device (automatic tile choice)
 int gemm_tile();
 // Split-BF16 tensor-core complex GEMM (STORE/ACCUM only), FP32 accumulation in TMEM (k_tc.cu): operands packed
 // into `pack` (tc_pack_bytes of the capacities), then streamed by bulk copies into the tensor cores.

@@ -104,3 +104,45 @@ def test_workload_sized_items_match_oracle(lib, prec, tol):
         # distance of the two states
         assert err < tol + 2 * np.sqrt(disc / n2) + 1e-6
     batch.close()
+
+
+def test_branch_tuner_and_shared_streams(lib, tmp_path):
+    # items whose contexts share one stream (PyTorch's stream pool repeats after 32 streams); the tuner times
+    # each branch count on copies, caches the choice, and the tuned batch (with range-path items, chi = 64,
+    # whose two factorisation paths are conditional graph nodes) agrees with the single-item steps
+    specs = [{"n": 6, "chi": 16, "r0": 0.1, "seed": 23110}, {"n": 7, "chi": 64, "r0": 0.07, "seed": 23111},
+             {"n": 6, "chi": 32, "r0": 0.15, "seed": 23112}, {"n": 7, "chi": 64, "r0": 0.2, "seed": 23113}]
+    enc = lib.Engine(n_sites=7, d=4, chi=64, w=16, dense=1 << 14)
+    ops = gpu_ops(lib, enc, sorted({s["n"] for s in specs}))
+    shared = torch.cuda.Stream()
+    items, engines, refs = [], [], []
+    for sp in specs:
+        n, chi = sp["n"], sp["chi"]
+        psi = lib.MPS(n, 4, chi)
+        enc.encode(torch.from_numpy(synth.batched_item_field(sp)).cuda(), n, "interleaved", psi, chi, 1e-10,
+                   stats=False)
+        items.append(psi)
+        refs.append(psi.clone())
+        engines.append(lib.Engine(n_sites=n, d=4, chi=chi, w=16, dense=0, stream=shared))
+    torch.cuda.synchronize()
+    Qs, Qds, Ds = ([ops[s["n"]][k] for s in specs] for k in range(3))
+    cache = str(tmp_path / "tune.txt")
+    copies = [it.clone() for it in items]
+    br, ms = lib.tune_branches(engines, copies, Qs, Qds, Ds, 0, 1e-10, "fp32", [1, 2, 4], cache_path=cache)
+    assert br in (1, 2, 4) and ms > 0
+    br2, _ = lib.tune_branches(engines, copies, Qs, Qds, Ds, 0, 1e-10, "fp32", [1, 2, 4], cache_path=cache)
+    assert br2 == br                                          # read back from the cache
+    batch = lib.Batch(engines, items, Qs, Qds, Ds, n_steps=1, chi_max=0, cutoff=1e-10, branches=br)
+    l0 = enc.launch_count()
+    batch.launch(2)
+    batch.sync()
+    assert enc.launch_count() > l0
+    for sp, ref in zip(specs, refs):
+        Q, Qd, D = ops[sp["n"]]
+        enc.fresnel_step(ref, "interleaved", Q, Qd, D, 2, sp["chi"], 1e-10, stats=False)
+    torch.cuda.synchronize()
+    for psi, ref in zip(items, refs):
+        a = [A.astype(np.complex128) for A in psi.to_numpy_sites()]
+        b = [A.astype(np.complex128) for A in ref.to_numpy_sites()]
+        assert dist(a, b) < 1e-5
+    batch.close()

@@ -41,6 +41,26 @@ def eng_small(lib):
 
 # ----------------------------------------------------------------------------- encode (TT-SVD)
 
+def test_encode_of_smooth_factors_matches_oracle(lib):
+    # 1-D encodes of the smooth phase factors of the 2^16 workload (fast-decaying spectra, most eigenvalues
+    # at the rounding level of the Gram): bonds and relative discarded weight of the oracle's TT-SVD
+    n = 16
+    fx, gy = synth.separable_phase_factors(n)
+    e = lib.Engine(n_sites=n, d=2, chi=32, w=2, dense=1 << n)
+    for v in (fx[0], fx[1], gy[0], gy[1]):
+        X = lib.MPS(n, 2, 32)
+        st = e.encode(torch.from_numpy(v.astype(np.complex64)).cuda(), n, "1d", X, 32, 1e-10)
+        v64 = v.astype(np.complex128)
+        n2 = float(np.vdot(v64, v64).real)
+        ref, eps = OS.tt_svd(OQ.dense_to_quantics(v64, "1d"), n, 2, 32, 1e-10)
+        assert max(abs(a - b) for a, b in zip(X.bonds(), OS.bonds(ref))) <= 1, (X.bonds(), OS.bonds(ref))
+        assert abs(st.discarded - sum(eps)) / n2 <= 1e-6 * sum(eps) / n2 + 1e-9
+        got = [A.astype(np.complex128) for A in X.to_numpy_sites()]
+        tol = 1e-5 + np.sqrt(st.discarded / n2) + np.sqrt(sum(eps) / n2)
+        d2 = OS.norm2(got) + OS.norm2(ref) - 2 * OS.overlap(got, ref).real
+        assert np.sqrt(max(d2, 0.0) / OS.norm2(ref)) < tol
+
+
 @pytest.mark.parametrize("layout,n", [("interleaved", 4), ("serial", 4), ("1d", 10), ("interleaved", 6)])
 def test_encode_untruncated_reconstructs(eng, lib, layout, n):
     E = synth.gaussian_beam_with_rectangles(n, seed=200 + n, waist=0.2) if layout != "1d" else \

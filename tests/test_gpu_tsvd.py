@@ -73,6 +73,16 @@ def test_rank_deficient_and_zero(eng):
     T = (A @ B).astype(np.complex64)
     U, C, st = eng.tsvd(torch.from_numpy(T).cuda(), 10 ** 6, 0.0)
     assert U.shape[1] == 5
+    # a rank-deficient matrix on the range-finder path: the sketch keeps its five live columns
+    A = rng.standard_normal((300, 5)) + 1j * rng.standard_normal((300, 5))
+    B = rng.standard_normal((5, 420)) + 1j * rng.standard_normal((5, 420))
+    T = (A @ B).astype(np.complex64)
+    U, C, st = eng.tsvd(torch.from_numpy(T).cuda(), 10 ** 6, 0.0)
+    U, C = U.cpu().numpy().astype(np.complex128), C.cpu().numpy().astype(np.complex128)
+    T64 = T.astype(np.complex128)
+    assert U.shape[1] == 5
+    assert np.linalg.norm(U @ C - T64) / np.linalg.norm(T64) < 2e-6
+    assert np.abs(U.conj().T @ U - np.eye(5)).max() < 2e-6
     Z = np.zeros((12, 9), np.complex64)
     U, C, st = eng.tsvd(torch.from_numpy(Z).cuda(), 10 ** 6, 0.0)
     assert U.shape[1] == 1 and st.discarded == 0.0
