@@ -335,6 +335,15 @@ qtn_status qtn_batch_tune_branches(int count, void* const* ctxs, qtn_mps* items,
  * small contractions of low-chi items).  QTN_ERR_ARG for any other value. */
 qtn_status qtn_set_gemm_tile(void* ctx, int tile);
 
+/* Eigen-solver of the truncation SVD (Sec. IV, App. A: the SVD of every truncation is taken through the
+ * eigenvectors of the Gram matrix).  The rough first eigen-solve of a truncation (whose basis the refinement
+ * solve then corrects) runs, for a live order r >= r_min (at most 160), as one-sided Jacobi over a cluster
+ * of 8 CTAs with the rotations accumulated into the eigenvector matrix; a smaller one, and every refinement
+ * solve, in a single CTA.  Process-wide (all contexts and devices); default 32; values below 2 are taken as 2 and
+ * values above 160 send every problem to the single CTA.  Takes effect for launches recorded after the
+ * call (graphs already recorded keep their choice). */
+qtn_status qtn_set_eig_cluster_min(int r_min);
+
 /* Autotuner of the GEMM tile: times one Fresnel step of `item` (after one step
  * of warm-up) with each tile, keeps the faster for the context and returns it
  * (tile_out, and its ms per step in ms_out when non-NULL).  The decision is

@@ -28,7 +28,9 @@ from . import mps as _mps
 from . import mpo as _mpo
 
 
-def zipup_lr(W, A, chi_max: int, cutoff: float):
+def zipup_lr(W, A, chi_max: int, cutoff: float, totals=None):
+    """Left-to-right zip-up; when `totals` is a list, the squared Frobenius norm of every factorised
+    two-site matrix is appended to it (the weight each local discarded weight is a part of)."""
     N = len(A)
     C = np.ones((1, 1, 1), dtype=np.complex128)
     out, eps = [], []
@@ -41,18 +43,20 @@ def zipup_lr(W, A, chi_max: int, cutoff: float):
         U, s, Vh = _mps.svd(T.reshape(x * t, b * k))
         r = _mps.keep_rank(s, chi_max, cutoff)
         eps.append(float(np.sum(s[r:] ** 2)))
+        if totals is not None:
+            totals.append(float(np.sum(s ** 2)))
         out.append(U[:, :r].reshape(x, t, r))
         C = (s[:r, None] * Vh[:r]).reshape(r, b, k)
     return out, eps
 
 
-def zipup(W, A, chi_max: int, cutoff: float, direction: str):
+def zipup(W, A, chi_max: int, cutoff: float, direction: str, totals=None):
     """Zip-up in the given direction ('lr' needs a right-canonical input, 'rl'
     a left-canonical one).  Returns (sites, eps) with eps in bond order."""
     if direction == "lr":
-        return zipup_lr(W, A, chi_max, cutoff)
+        return zipup_lr(W, A, chi_max, cutoff, totals)
     if direction == "rl":
-        out, eps = zipup_lr(_mpo.mirror(W), _mps.mirror(A), chi_max, cutoff)
+        out, eps = zipup_lr(_mpo.mirror(W), _mps.mirror(A), chi_max, cutoff, totals)
         return _mps.mirror(out), eps[::-1]
     raise ValueError(direction)
 

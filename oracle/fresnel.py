@@ -86,9 +86,10 @@ def step_passes(layout: str, n: int, Q, Qd, D):
     return passes
 
 
-def apply_sequence(passes, sites, canon: str, chi_max: int, cutoff: float):
+def apply_sequence(passes, sites, canon: str, chi_max: int, cutoff: float, totals=None):
     """Apply embedded MPOs in order by zip-up with alternating directions.
-    Returns (sites, canon, total discarded weight)."""
+    Returns (sites, canon, total discarded weight); `totals` (a list) collects
+    the squared norms of the factorised matrices."""
     A = sites
     if canon == "none":
         A = _mps.left_canonicalize(A)
@@ -96,20 +97,20 @@ def apply_sequence(passes, sites, canon: str, chi_max: int, cutoff: float):
     disc = 0.0
     for W in passes:
         direction = "rl" if canon == "left" else "lr"
-        A, eps = _apply.zipup(W, A, chi_max, cutoff, direction)
+        A, eps = _apply.zipup(W, A, chi_max, cutoff, direction, totals)
         disc += sum(eps)
         canon = "right" if direction == "rl" else "left"
     return A, canon, disc
 
 
 def fresnel_mps(sites, layout: str, n: int, c: float, chi_max: int, cutoff: float,
-                canon: str = "none", n_steps: int = 1, ops=None):
+                canon: str = "none", n_steps: int = 1, ops=None, totals=None):
     """n_steps Fresnel steps on an MPS.  Returns (sites, canon, discarded)."""
     Q, Qd, D = ops if ops is not None else step_operators(n, c)
     passes = step_passes(layout, n, Q, Qd, D)
     disc = 0.0
     A = sites
     for _ in range(n_steps):
-        A, canon, d = apply_sequence(passes, A, canon, chi_max, cutoff)
+        A, canon, d = apply_sequence(passes, A, canon, chi_max, cutoff, totals)
         disc += d
     return A, canon, disc

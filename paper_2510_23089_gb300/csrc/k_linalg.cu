@@ -17,6 +17,7 @@
 #include <stdlib.h>
 
 #include <atomic>
+#include <climits>
 
 #include "qtn_internal.cuh"
 
@@ -682,13 +683,13 @@ __global__ void __launch_bounds__(EIG_THREADS, 1)
 k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restrict__ U, Dim ldud,
              double* __restrict__ lam, const int* Rc, int* Rw, int max_sweeps,   // Rc, Rw: one register array
              double* __restrict__ ledger, int guard_reg, int guard_val, double* __restrict__ prof, float tol,
-             float dead_rel, int report_nonconv) {
+             float dead_rel, int report_nonconv, int r_limit) {
     if (guard_reg >= 0 && Rc[guard_reg] != guard_val) return;
     extern __shared__ float2 W[];                // column-major, W[j*EIG_RS + i]
     __shared__ int rotated, sig_rotated;
     const int r = rdim.eval(Rc);
     const long long ld = ldd.eval(Rc), ldu = ldud.eval(Rc);
-    if (r <= 0) return;
+    if (r <= 0 || r >= r_limit) return;   // r >= r_limit: solved by the cluster kernel
     __shared__ double gscale;
     __shared__ unsigned long long n_pairs, n_rot;
     const int tid = threadIdx.x;
@@ -785,16 +786,36 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
 
 cudaError_t launch_eig(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, double* lam, const int* R,
                        int r_cap, int max_sweeps, double* ledger, cudaStream_t s, int guard_reg, int guard_val,
-                       float tol, float dead_rel, bool report_nonconv) {
+                       float tol, float dead_rel, bool report_nonconv,
+                       bool cluster_ok) {
     const size_t smem = (size_t)EIG_MAX * EIG_RS * sizeof(float2);
-    count_launch(PROF_EIG, s, true);
     double* prof = g_prof_ledger ? g_prof_ledger + L_PROF_EIG : nullptr;
-    (void)r_cap;
+    // A rough first solve whose basis a refinement corrects (cluster_ok) with r at or above the cluster threshold
+    // runs on the cluster kernel (k_eig_cluster.cu: rotations accumulated into an orthonormal basis); everything
+    // else in one CTA, whose eigenvectors are the normalised columns of G V (the product with G filters the
+    // rounding-level mixing of directions whose eigenvalues are near the FP32 resolution of G), orthonormalised
+    // in descending order.  When the capacity allows either, both are launched and the one whose range does not
+    // hold the live r returns at once.
+    const int r_min = eig_cluster_min();
+    const bool cl = cluster_ok && (r_cap >= r_min);
+    count_launch(PROF_EIG, s, true);
     k_eig_jacobi<<<1, EIG_THREADS, smem, s>>>(G, ld, r, U, ldu, lam, R, (int*)R, max_sweeps, ledger, guard_reg,
-                                               guard_val, prof, tol, dead_rel, report_nonconv ? 1 : 0);
+                                               guard_val, prof, tol, dead_rel, report_nonconv ? 1 : 0,
+                                               cl ? r_min : INT_MAX);
     count_launch(PROF_EIG, s, false);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !cl) return e;
+    count_launch(PROF_EIG, s, true);
+    e = launch_eig_cluster(G, ld, r, U, ldu, lam, R, max_sweeps, s, guard_reg, guard_val, prof, tol, report_nonconv,
+                           r_min);
+    count_launch(PROF_EIG, s, false);
+    return e;
 }
+
+// Smallest live r solved by the cluster kernel (process-wide).
+static std::atomic<int> g_eig_cluster_min{32};
+int eig_cluster_min() { return g_eig_cluster_min.load(std::memory_order_relaxed); }
+void set_eig_cluster_min(int r) { g_eig_cluster_min.store(r < 2 ? 2 : r, std::memory_order_relaxed); }
 
 // ------------------------------------------------------------------ launch accounting / profiling
 double* g_prof_ledger = nullptr;
@@ -864,8 +885,10 @@ void prof_read(int cls, double* ms, long long* launches) {
 
 // ------------------------------------------------------------------ per-device kernel attributes
 cudaError_t configure_eig_kernel() {
-    return cudaFuncSetAttribute(k_eig_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)((size_t)EIG_MAX * EIG_RS * sizeof(float2)));
+    cudaError_t e = cudaFuncSetAttribute(k_eig_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)((size_t)EIG_MAX * EIG_RS * sizeof(float2)));
+    if (e == cudaSuccess) e = configure_eig_cluster_kernel();
+    return e;
 }
 
 }  // namespace qtn

@@ -348,7 +348,7 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
     k_trace<<<1, 256, 0, s>>>(w.G64, gld, io.m, w.R, w.ledger);
     CKL();
     CK(launch_eig(w.G64, dc(gld), io.m, w.U, dc(gld), w.lam, w.R, std::min(mc, EIG_MAX), sweeps1, w.ledger, s,
-                  R_RAND, 0, tol1, dead1, false));
+                  R_RAND, 0, tol1, dead1, false, true));
     {
         GemmDesc g{};
         g.A = mat(w.U, dc(gld), dc(1), 1);
@@ -522,7 +522,7 @@ static qtn_status tsvd(Ctx* c, Ws& w, const TsvdIO& io, const qtn_trunc& tr, int
             if ((st = gram(w.G32, Pl, ncol, ncol, pc, 1, false, cwid))) return st;
         }
         CK(launch_eig(w.G64, dc(gld), Pl, UB, dc(pc), w.lam, w.R, pc, sweeps1, w.ledger, s, R_RAND, 1, tol1, dead1,
-                      false));
+                      false, true));
         {   // U = Q U_B  (m x p, column-major with leading dimension gld)
             GemmDesc g{};
             g.A = mat(Qb, dc(pc), dc(1));
@@ -1620,6 +1620,11 @@ qtn_status qtn_batch_tune_branches(int count, void* const* ctxs, qtn_mps* items,
             fprintf(f, "%s %d %.6f\n", key, best, best_ms);
             fclose(f);
         }
+    return QTN_OK;
+}
+
+qtn_status qtn_set_eig_cluster_min(int r_min) {
+    set_eig_cluster_min(r_min);
     return QTN_OK;
 }
 

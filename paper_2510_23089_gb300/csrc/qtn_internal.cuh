@@ -206,9 +206,17 @@ size_t tc_pack_bytes(int max_m, int max_n, int max_k);
 cudaError_t launch_gemm_tc(const GemmDesc& d, int max_m, int max_n, int max_k, const int* R, void* pack,
                            size_t pack_bytes, int sm_count, cudaStream_t s);
 cudaError_t launch_refine_basis(const double2* G, Dim ld, Dim r, float2* V, int ldv, const int* R, cudaStream_t s);
+// One-sided Jacobi over a cluster of 8 CTAs with accumulated rotations (k_eig_cluster.cu); runs when
+// r_min <= r (live) <= EIG_MAX and R[guard_reg] == guard_val.
+cudaError_t launch_eig_cluster(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, double* lam, const int* R,
+                               int max_sweeps, cudaStream_t s, int guard_reg, int guard_val, double* prof, float tol,
+                               bool report_nonconv, int r_min);
+cudaError_t configure_eig_cluster_kernel();
+int eig_cluster_min();
+void set_eig_cluster_min(int r);
 cudaError_t launch_eig(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, double* lam, const int* R,
                        int r_cap, int max_sweeps, double* ledger, cudaStream_t s, int guard_reg = -1, int guard_val = 0,
-                       float tol = 1e-6f, float dead_rel = 0.f, bool report_nonconv = true);
+                       float tol = 1e-6f, float dead_rel = 0.f, bool report_nonconv = true, bool cluster_ok = false);
 
 }  // namespace qtn
 

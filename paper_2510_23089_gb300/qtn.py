@@ -39,6 +39,7 @@ EXPORTS = (
     "qtn_workspace_init", "qtn_check", "qtn_build_bessel_mpo", "qtn_build_pauliz_mpo",
     "qtn_reverse_sites", "qtn_psf", "qtn_convolve", "qtn_astf_field", "qtn_transfer_step", "qtn_project_apply",
     "qtn_batch_stream", "qtn_set_gemm_tile", "qtn_tune_gemm_tile", "qtn_batch_tune_branches",
+    "qtn_set_eig_cluster_min",
 )
 
 
@@ -112,6 +113,7 @@ def load_library(path: str = LIB_PATH):
         "qtn_batch_tune_branches": [I, ctypes.POINTER(P), mp, op, op, op, tr, ctypes.POINTER(P), ctypes.POINTER(S),
                                     ctypes.POINTER(I), I, ctypes.c_char_p, ctypes.POINTER(I), ctypes.POINTER(D)],
         "qtn_set_gemm_tile": [P, I],
+        "qtn_set_eig_cluster_min": [I],
         "qtn_tune_gemm_tile": [P, mp, op, op, op, tr, P, S, ctypes.c_char_p, ctypes.POINTER(I), ctypes.POINTER(D)],
         "qtn_batch_launch": [P, I],
         "qtn_batch_sync": [P],
@@ -459,6 +461,10 @@ class Engine:
                                           ctypes.byref(T.c), self.trunc(chi_max, cutoff),
                                           ctypes.byref(st) if stats else None, *self._ws()), "qtn_transfer_step")
         return _stats(st) if stats else None
+
+    def set_eig_cluster_min(self, r_min: int):
+        """Smallest problem order solved by the cluster eigen-solver (process-wide; 161 disables it)."""
+        _check(self.lib.qtn_set_eig_cluster_min(int(r_min)), "qtn_set_eig_cluster_min")
 
     def set_gemm_tile(self, tile: int):
         _check(self.lib.qtn_set_gemm_tile(self.ctx, int(tile)), "qtn_set_gemm_tile")

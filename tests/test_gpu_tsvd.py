@@ -86,3 +86,27 @@ def test_rank_deficient_and_zero(eng):
     Z = np.zeros((12, 9), np.complex64)
     U, C, st = eng.tsvd(torch.from_numpy(Z).cuda(), 10 ** 6, 0.0)
     assert U.shape[1] == 1 and st.discarded == 0.0
+
+
+@pytest.mark.parametrize("cluster_min", [2, 161])   # every order on the cluster solver / on the single CTA
+@pytest.mark.parametrize("m,n,decay,chi", [(12, 40, 0.1, 8), (33, 70, 0.0, 20), (48, 48, 0.3, 30),
+                                           (128, 256, 0.05, 40), (160, 200, 0.05, 64), (512, 768, 0.02, 128)])
+def test_both_eigen_solvers_meet_eckart_young(eng, cluster_min, m, n, decay, chi):
+    T = make(m, n, decay, seed=11 * m + n)
+    T64 = T.astype(np.complex128)
+    s = np.linalg.svd(T64, compute_uv=False)
+    n2 = float((s ** 2).sum())
+    eng.set_eig_cluster_min(cluster_min)
+    try:
+        U, C, st = eng.tsvd(torch.from_numpy(T).cuda(), chi, 0.0)
+        Uf, Cf, stf = eng.tsvd(torch.from_numpy(T).cuda(), 10 ** 6, 1e-12)
+    finally:
+        eng.set_eig_cluster_min(32)
+    U, C = U.cpu().numpy().astype(np.complex128), C.cpu().numpy().astype(np.complex128)
+    assert U.shape[1] == chi
+    assert np.abs(U.conj().T @ U - np.eye(chi)).max() < 2e-6
+    assert abs(np.linalg.norm(U @ C - T64) ** 2 - st.discarded) <= 1e-5 * n2
+    assert abs(st.discarded - float((s[chi:] ** 2).sum())) <= 1e-6 * n2
+    if min(m, n) <= 160:   # beyond, the range finder keeps a 160-dimensional subspace
+        Uf, Cf = Uf.cpu().numpy().astype(np.complex128), Cf.cpu().numpy().astype(np.complex128)
+        assert np.linalg.norm(Uf @ Cf - T64) / np.linalg.norm(T64) < 2e-6

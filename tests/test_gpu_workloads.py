@@ -10,10 +10,12 @@
   transfer function, sampled by qtn_amplitudes (P9; aliasing and wrap-around terms are below 1e-10 here).
 
 Tolerance (FP32 path): relative L2 within 1e-5 + sqrt(eps_gpu) + sqrt(eps_orc), eps the relative
-discarded weights each side reports; relative discarded weights agree within 1e-6 per step.  Where the zip-up
-discards a large sum of local weights (the 1024^2 step at chi = 64 discards local weights of 0.75 |psi|^2: its
-non-isometric environments make them much larger than the true error), the FP32 weights are resolved relative
-to the unfoldings they come from, and the sums agree within 1e-4 of themselves."""
+discarded weights each side reports; discarded weights agree within 1e-6 relative.  Each local discarded
+weight of a zip-up is part of the weight of the two-site matrix it is taken from, and an FP32 factorisation
+resolves it to 1e-6 of that matrix's weight (the Eckart-Young check of the single factorisation); the zip-up's
+environments are not isometric, so those weights can exceed |psi|^2 many times (the 1024^2 step at chi = 64
+factorises matrices of up to ~60 |psi|^2).  The sums are compared within 1e-6 of |psi|^2 plus the weights of
+the oracle's factorised matrices."""
 import os
 import sys
 
@@ -64,7 +66,8 @@ def test_fresnel_step_1024(lib):
 
     sites, eps_e = OS.tt_svd(OQ.dense_to_quantics(E64, "interleaved"), n, 4, chi, cut)
     ops = OF.step_operators(n, c, qft=OM.qft_mpo_layers(n, 1e-12), phase_cutoff=1e-12)
-    out, canon, disc = OF.fresnel_mps(sites, "interleaved", n, c, chi, cut, canon="left", ops=ops)
+    totals = []
+    out, canon, disc = OF.fresnel_mps(sites, "interleaved", n, c, chi, cut, canon="left", ops=ops, totals=totals)
     ref = OQ.quantics_to_dense(OS.to_vector(out), n, "interleaved")
     eg = (st_e.discarded + st.discarded) / n2
     eo = (sum(eps_e) + disc) / n2
@@ -72,7 +75,8 @@ def test_fresnel_step_1024(lib):
     print(f"n=10 step: rel {err:.3e} eps_gpu {eg:.2e} eps_orc {eo:.2e} bonds {psi.bonds()} vs {OS.bonds(out)}")
     assert err <= 1e-5 + np.sqrt(eg) + np.sqrt(eo)
     assert abs(st_e.discarded - sum(eps_e)) <= 1e-6 * n2
-    assert abs(st.discarded - disc) <= 1e-6 * n2 + 1e-4 * disc
+    print(f"n=10 step: discarded gpu {st.discarded:.6f} oracle {disc:.6f}, factorised weight {sum(totals):.1f}")
+    assert abs(st.discarded - disc) <= 1e-6 * (n2 + sum(totals))
     # against the exact dense propagation (matrix DFTs): the truncated step stays within its own budget
     exact = OF.fresnel_dense(E64, c)
     print(f"n=10 step vs exact dense: gpu {rel(got, exact):.3e}, oracle {rel(ref, exact):.3e}")

@@ -437,6 +437,26 @@ def test_apply_naive_error_equals_discarded_weight():
     assert abs(np.linalg.norm(OS.to_vector(out) - y) ** 2 - sum(eps)) < 1e-12 * np.linalg.norm(y) ** 2
 
 
+def test_zipup_factorised_weights_of_an_isometric_chain_equal_the_norm():
+    # the identity operator on a canonical state: everything left of a bond is an isometry (the new sites)
+    # and everything right of it too (the untouched canonical sites), so every factorised two-site matrix
+    # carries exactly the squared norm of the state; its discarded parts are parts of that weight
+    n = 6
+    ident = OM.identity(n)
+    raw = synth.random_mps_sites([1, 2, 4, 8, 4, 2, 1], 2, seed=905, decay=0.3)
+    n2 = OS.norm2(raw)
+    for direction, canon in (("lr", OS.right_canonicalize), ("rl", OS.left_canonicalize)):
+        totals = []
+        out, eps = OA.zipup(ident, canon(raw), 1 << 10, 0.0, direction, totals)
+        assert len(totals) == n - 1
+        assert np.allclose(totals, n2, rtol=1e-12, atol=0.0)
+        assert rel(OS.to_vector(out), OS.to_vector(raw)) < 1e-12
+    # with truncation the discarded weights stay within the factorised weights
+    totals = []
+    out, eps = OA.zipup(ident, OS.right_canonicalize(raw), 2, 0.0, "lr", totals)
+    assert all(0.0 <= e <= t for e, t in zip(eps, totals)) and sum(eps) > 0.0
+
+
 def test_schmidt_spectra_match_dense_unfoldings():
     # the Schmidt values at bond k are the singular values of the (d^k) x (d^(N-k)) unfolding of the vector
     bonds = [1, 4, 9, 7, 3, 1]
