@@ -336,10 +336,10 @@ qtn_status qtn_batch_tune_branches(int count, void* const* ctxs, qtn_mps* items,
 qtn_status qtn_set_gemm_tile(void* ctx, int tile);
 
 /* Eigen-solver of the truncation SVD (Sec. IV, App. A: the SVD of every truncation is taken through the
- * eigenvectors of the Gram matrix).  The rough first eigen-solve of a truncation (whose basis the refinement
- * solve then corrects) runs, for a live order r >= r_min (at most 160), as one-sided Jacobi over a cluster
- * of 8 CTAs with the rotations accumulated into the eigenvector matrix; a smaller one, and every refinement
- * solve, in a single CTA.  Process-wide (all contexts and devices); default 32; values below 2 are taken as 2 and
+ * eigenvectors of the Gram matrix).  For a live order r >= r_min (at most 160) the Jacobi sweeps run over a
+ * cluster of 8 CTAs: the rough first solve of a truncation accumulates its rotations into an orthonormal
+ * basis, the refinement solve hands its rotated columns to a one-CTA kernel that normalises and
+ * orthonormalises them; a smaller problem runs entirely in a single CTA.  Process-wide (all contexts and devices); default 32; values below 2 are taken as 2 and
  * values above 160 send every problem to the single CTA.  Takes effect for launches recorded after the
  * call (graphs already recorded keep their choice). */
 qtn_status qtn_set_eig_cluster_min(int r_min);

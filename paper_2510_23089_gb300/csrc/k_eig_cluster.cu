@@ -45,8 +45,9 @@ __device__ __forceinline__ void ecl_circle(int u, int k, int n, int& i, int& j) 
 }
 
 // Orthogonalises the W columns wx, wy (rows lane, lane + 32, ...) with one plane rotation when their inner
-// product exceeds tol of their norms, applying the same rotation to the V columns vx, vy.  The sums are
-// butterfly reductions, so every lane holds the same bits and takes the same branch.
+// product exceeds tol of their norms, applying the same rotation to the V columns vx, vy when ACCV.  The sums
+// are butterfly reductions, so every lane holds the same bits and takes the same branch.
+template <bool ACCV>
 __device__ __forceinline__ void ecl_pair(float2* __restrict__ wx, float2* __restrict__ wy, float2* __restrict__ vx,
                                          float2* __restrict__ vy, int r, int lane, float tol, int& rotated,
                                          int& sig_rotated, unsigned long long& n_pairs, unsigned long long& n_rot) {
@@ -82,17 +83,20 @@ __device__ __forceinline__ void ecl_pair(float2* __restrict__ wx, float2* __rest
         const float2 x = wx[row], y = wy[row];
         wx[row] = make_float2(fmaf(cs, x.x, -fmaf(pr, y.x, pi * y.y)), fmaf(cs, x.y, -fmaf(pr, y.y, -pi * y.x)));
         wy[row] = make_float2(fmaf(cs, y.x, fmaf(pr, x.x, -pi * x.y)), fmaf(cs, y.y, fmaf(pr, x.y, pi * x.x)));
-        const float2 u = vx[row], v = vy[row];
-        vx[row] = make_float2(fmaf(cs, u.x, -fmaf(pr, v.x, pi * v.y)), fmaf(cs, u.y, -fmaf(pr, v.y, -pi * v.x)));
-        vy[row] = make_float2(fmaf(cs, v.x, fmaf(pr, u.x, -pi * u.y)), fmaf(cs, v.y, fmaf(pr, u.y, pi * u.x)));
+        if (ACCV) {
+            const float2 u = vx[row], v = vy[row];
+            vx[row] = make_float2(fmaf(cs, u.x, -fmaf(pr, v.x, pi * v.y)), fmaf(cs, u.y, -fmaf(pr, v.y, -pi * v.x)));
+            vy[row] = make_float2(fmaf(cs, v.x, fmaf(pr, u.x, -pi * u.y)), fmaf(cs, v.y, fmaf(pr, u.y, pi * u.x)));
+        }
     }
     ++n_rot;
     rotated = 1;
     if (ab2 > ECL_SIG * ECL_SIG) sig_rotated = 1;
 }
 
-// Copies the BS live columns (W and V) and the column indices of `src` into buffer `dst_buf` of CTA `dst_cta`
-// (its own shared memory when dst_cta is this CTA).
+// Copies the BS live columns (W, and V when ACCV) and the column indices of `src` into buffer `dst_buf` of CTA
+// `dst_cta` (its own shared memory when dst_cta is this CTA).
+template <bool ACCV>
 __device__ __forceinline__ void ecl_send(cg::cluster_group& cluster, const EclBlock& src, EclBlock* buf, int dst_buf,
                                          int dst_cta, int BS, int tid) {
     EclBlock* dst = cluster.map_shared_rank(buf + dst_buf, dst_cta);
@@ -100,13 +104,18 @@ __device__ __forceinline__ void ecl_send(cg::cluster_group& cluster, const EclBl
     float4* d4 = reinterpret_cast<float4*>(dst);
     constexpr int per_col = ECL_LD / 2;                        // float4 per column
     constexpr int per_mtx = ECL_BS * per_col;                  // float4 offset of V
-    for (int e = tid; e < 2 * BS * per_col; e += ECL_THREADS) {
+    for (int e = tid; e < (ACCV ? 2 : 1) * BS * per_col; e += ECL_THREADS) {
         const int mtx = e / (BS * per_col), rem = e - mtx * (BS * per_col);
         d4[mtx * per_mtx + rem] = s4[mtx * per_mtx + rem];
     }
     if (tid < 16) dst->id[tid] = src.id[tid];
 }
 
+// ACCV: rotations accumulated into V and the sorted eigenvectors written to U (columns by descending
+// eigenvalue) with the eigenvalues in lam.  !ACCV: the rotated columns of W = G V / s written unsorted to U
+// (column j at U + j ldu, in the units of G / s) for k_eig_finish, which takes the eigenvectors as their
+// normalised columns.
+template <bool ACCV>
 __global__ void __cluster_dims__(ECL_C, 1, 1) __launch_bounds__(ECL_THREADS, 1)
 k_eig_cluster(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restrict__ U, Dim ldud,
               double* __restrict__ lam, const int* Rc, int* Rw, int max_sweeps, int guard_reg, int guard_val,
@@ -153,7 +162,7 @@ k_eig_cluster(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restri
                 if (row == j) vv = make_float2(1.f, 0.f);
             }
             B.W[k][row] = wv;
-            B.V[k][row] = vv;
+            if (ACCV) B.V[k][row] = vv;
         }
     }
     __syncthreads();
@@ -177,7 +186,8 @@ k_eig_cluster(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restri
                         int i, j;
                         ecl_circle(u, warp % half, BSe, i, j);
                         if (i < BS && j < BS && Z.id[i] >= 0 && Z.id[j] >= 0)
-                            ecl_pair(Z.W[i], Z.W[j], Z.V[i], Z.V[j], r, lane, tol, my_rot, my_sig, n_pairs, n_rot);
+                            ecl_pair<ACCV>(Z.W[i], Z.W[j], Z.V[i], Z.V[j], r, lane, tol, my_rot, my_sig, n_pairs,
+                                           n_rot);
                     }
                     __syncthreads();
                 }
@@ -186,7 +196,7 @@ k_eig_cluster(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restri
                 if (warp < BS) {
                     const int i = warp, j = (warp + s) % BS;
                     if (X.id[i] >= 0 && Y.id[j] >= 0)
-                        ecl_pair(X.W[i], Y.W[j], X.V[i], Y.V[j], r, lane, tol, my_rot, my_sig, n_pairs, n_rot);
+                        ecl_pair<ACCV>(X.W[i], Y.W[j], X.V[i], Y.V[j], r, lane, tol, my_rot, my_sig, n_pairs, n_rot);
                 }
                 __syncthreads();
             }
@@ -207,12 +217,12 @@ k_eig_cluster(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restri
             // becomes its bottom), bottom blocks to the previous CTA (CTA 0's bottom becomes CTA 1's top).
             const int nb = 1 - par;
             if (q == 0) {
-                ecl_send(cluster, X, buf, 2 * nb, 0, BS, tid);
-                ecl_send(cluster, Y, buf, 2 * nb, 1, BS, tid);
+                ecl_send<ACCV>(cluster, X, buf, 2 * nb, 0, BS, tid);
+                ecl_send<ACCV>(cluster, Y, buf, 2 * nb, 1, BS, tid);
             } else {
-                if (q < ECL_C - 1) ecl_send(cluster, X, buf, 2 * nb, q + 1, BS, tid);
-                else ecl_send(cluster, X, buf, 2 * nb + 1, q, BS, tid);
-                ecl_send(cluster, Y, buf, 2 * nb + 1, q - 1, BS, tid);
+                if (q < ECL_C - 1) ecl_send<ACCV>(cluster, X, buf, 2 * nb, q + 1, BS, tid);
+                else ecl_send<ACCV>(cluster, X, buf, 2 * nb + 1, q, BS, tid);
+                ecl_send<ACCV>(cluster, Y, buf, 2 * nb + 1, q - 1, BS, tid);
             }
             cluster.sync();
             par = nb;
@@ -228,6 +238,16 @@ k_eig_cluster(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restri
         if (tid == 0) { rot_s = 0; sig_s = 0; }
         my_rot = my_sig = 0;
     }
+    if (!ACCV) {   // the rotated columns of W, unsorted, for the finishing kernel
+        for (int h = 0; h < 2; ++h) {
+            const EclBlock& B = buf[2 * par + h];
+            for (int e = tid; e < BS * r; e += ECL_THREADS) {
+                const int k = e / r, row = e - k * r;
+                const int j = B.id[k];
+                if (j >= 0) U[(long long)j * ldu + row] = B.W[k][row];
+            }
+        }
+    } else {
     // eigenvalues: column norms of W (FP64 sums) in the units of G, published to every CTA
     for (int h = 0; h < 2; ++h) {
         EclBlock& B = buf[2 * par + h];
@@ -266,8 +286,9 @@ k_eig_cluster(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restri
             if (lane == 0) lam[rk] = v;
         }
     }
+    }
     if (prof != nullptr && lane == 0 && (n_pairs | n_rot))
-        atomicAdd(prof, 8.0 * r * (double)n_pairs + 48.0 * r * (double)n_rot);
+        atomicAdd(prof, 8.0 * r * (double)n_pairs + (ACCV ? 48.0 : 24.0) * r * (double)n_rot);
     if (q == 0 && tid == 0) {
         atomicMax(&Rw[R_SWEEPS], sweep);
         // unconverged only when the last sweep still rotated a pair above the rounding level of the scaled Gram
@@ -277,14 +298,24 @@ k_eig_cluster(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restri
 
 cudaError_t launch_eig_cluster(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, double* lam, const int* R,
                                int max_sweeps, cudaStream_t s, int guard_reg, int guard_val, double* prof, float tol,
-                               bool report_nonconv, int r_min) {
-    k_eig_cluster<<<ECL_C, ECL_THREADS, ECL_SMEM, s>>>(G, ld, r, U, ldu, lam, R, (int*)R, max_sweeps, guard_reg,
-                                                      guard_val, prof, tol, report_nonconv ? 1 : 0, r_min);
+                               bool report_nonconv, int r_min, bool accumulate) {
+    if (accumulate)
+        k_eig_cluster<true><<<ECL_C, ECL_THREADS, ECL_SMEM, s>>>(G, ld, r, U, ldu, lam, R, (int*)R, max_sweeps,
+                                                                guard_reg, guard_val, prof, tol, report_nonconv ? 1 : 0,
+                                                                r_min);
+    else
+        k_eig_cluster<false><<<ECL_C, ECL_THREADS, ECL_SMEM, s>>>(G, ld, r, U, ldu, lam, R, (int*)R, max_sweeps,
+                                                                 guard_reg, guard_val, prof, tol,
+                                                                 report_nonconv ? 1 : 0, r_min);
     return cudaGetLastError();
 }
 
 cudaError_t configure_eig_cluster_kernel() {
-    return cudaFuncSetAttribute(k_eig_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ECL_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_eig_cluster<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ECL_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_eig_cluster<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ECL_SMEM);
+    return e;
 }
 
 }  // namespace qtn

@@ -784,20 +784,57 @@ k_eig_jacobi(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restric
     }
 }
 
+// Eigenvectors of the rotated columns of W left in U by the cluster sweeps (column j at U + j ldu, in the units of
+// G / s, s the largest diagonal entry of G): the same finishing step as k_eig_jacobi, on one CTA.
+__global__ void __launch_bounds__(EIG_THREADS, 1)
+k_eig_finish(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* U, Dim ldud, double* __restrict__ lam,
+             const int* __restrict__ Rc, int guard_reg, int guard_val, float dead_rel, int r_min,
+             double* __restrict__ prof) {
+    if (guard_reg >= 0 && Rc[guard_reg] != guard_val) return;
+    const int r = rdim.eval(Rc);
+    if (r < r_min || r < 2 || r > EIG_MAX) return;
+    extern __shared__ float2 W[];
+    __shared__ double gscale;
+    const long long ld = ldd.eval(Rc), ldu = ldud.eval(Rc);
+    const int tid = threadIdx.x;
+    if (tid < 32) {
+        double mx = 0.0;
+        for (int i = tid; i < r; i += 32) mx = fmax(mx, fabs(G[(long long)i * ld + i].x));
+        for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        if (tid == 0) gscale = (mx > 0.0 && isfinite(mx)) ? mx : 1.0;
+    }
+    for (int e = tid; e < r * r; e += EIG_THREADS) {
+        const int j = e / r, i = e - j * r;
+        W[j * EIG_RS + i] = U[(long long)j * ldu + i];
+    }
+    __syncthreads();
+    eig_finish(W, r, gscale, U, ldu, lam, dead_rel);
+    if (prof != nullptr && tid == 0) atomicAdd(prof, 8.0 * (double)r * r * r);
+}
+
+cudaError_t launch_eig_finish(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, double* lam, const int* R,
+                              cudaStream_t s, int guard_reg, int guard_val, float dead_rel, int r_min) {
+    const size_t smem = (size_t)EIG_MAX * EIG_RS * sizeof(float2);
+    double* prof = g_prof_ledger ? g_prof_ledger + L_PROF_EIG : nullptr;
+    k_eig_finish<<<1, EIG_THREADS, smem, s>>>(G, ld, r, U, ldu, lam, R, guard_reg, guard_val, dead_rel, r_min, prof);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_eig(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, double* lam, const int* R,
                        int r_cap, int max_sweeps, double* ledger, cudaStream_t s, int guard_reg, int guard_val,
                        float tol, float dead_rel, bool report_nonconv,
-                       bool cluster_ok) {
+                       bool rough_basis) {
     const size_t smem = (size_t)EIG_MAX * EIG_RS * sizeof(float2);
     double* prof = g_prof_ledger ? g_prof_ledger + L_PROF_EIG : nullptr;
-    // A rough first solve whose basis a refinement corrects (cluster_ok) with r at or above the cluster threshold
-    // runs on the cluster kernel (k_eig_cluster.cu: rotations accumulated into an orthonormal basis); everything
-    // else in one CTA, whose eigenvectors are the normalised columns of G V (the product with G filters the
-    // rounding-level mixing of directions whose eigenvalues are near the FP32 resolution of G), orthonormalised
-    // in descending order.  When the capacity allows either, both are launched and the one whose range does not
+    // r at or above the cluster threshold: the sweeps run on the cluster kernel (k_eig_cluster.cu).  A rough first
+    // solve whose basis a refinement corrects (rough_basis) takes its eigenvectors from rotations accumulated into
+    // an orthonormal basis; otherwise the eigenvectors are the normalised columns of G V (the product with G filters
+    // the rounding-level mixing of directions whose eigenvalues are near the FP32 resolution of G), orthonormalised
+    // in descending order by k_eig_finish on one CTA.  Below the threshold everything runs in one CTA
+    // (k_eig_jacobi).  When the capacity allows either, both paths are launched and the one whose range does not
     // hold the live r returns at once.
     const int r_min = eig_cluster_min();
-    const bool cl = cluster_ok && (r_cap >= r_min);
+    const bool cl = (r_cap >= r_min);
     count_launch(PROF_EIG, s, true);
     k_eig_jacobi<<<1, EIG_THREADS, smem, s>>>(G, ld, r, U, ldu, lam, R, (int*)R, max_sweeps, ledger, guard_reg,
                                                guard_val, prof, tol, dead_rel, report_nonconv ? 1 : 0,
@@ -807,7 +844,11 @@ cudaError_t launch_eig(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, doub
     if (e != cudaSuccess || !cl) return e;
     count_launch(PROF_EIG, s, true);
     e = launch_eig_cluster(G, ld, r, U, ldu, lam, R, max_sweeps, s, guard_reg, guard_val, prof, tol, report_nonconv,
-                           r_min);
+                           r_min, rough_basis);
+    count_launch(PROF_EIG, s, false);
+    if (e != cudaSuccess || rough_basis) return e;
+    count_launch(PROF_EIG, s, true);
+    e = launch_eig_finish(G, ld, r, U, ldu, lam, R, s, guard_reg, guard_val, dead_rel, r_min);
     count_launch(PROF_EIG, s, false);
     return e;
 }
@@ -887,6 +928,9 @@ void prof_read(int cls, double* ms, long long* launches) {
 cudaError_t configure_eig_kernel() {
     cudaError_t e = cudaFuncSetAttribute(k_eig_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)((size_t)EIG_MAX * EIG_RS * sizeof(float2)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_eig_finish, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((size_t)EIG_MAX * EIG_RS * sizeof(float2)));
     if (e == cudaSuccess) e = configure_eig_cluster_kernel();
     return e;
 }

@@ -210,13 +210,17 @@ cudaError_t launch_refine_basis(const double2* G, Dim ld, Dim r, float2* V, int 
 // r_min <= r (live) <= EIG_MAX and R[guard_reg] == guard_val.
 cudaError_t launch_eig_cluster(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, double* lam, const int* R,
                                int max_sweeps, cudaStream_t s, int guard_reg, int guard_val, double* prof, float tol,
-                               bool report_nonconv, int r_min);
+                               bool report_nonconv, int r_min, bool accumulate);
+// Eigenvectors from the rotated columns of W that k_eig_cluster<false> left in U (normalised, orthonormalised in
+// descending-eigenvalue order, completed), one CTA; runs when r_min <= r <= EIG_MAX and R[guard_reg] == guard_val.
+cudaError_t launch_eig_finish(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, double* lam, const int* R,
+                              cudaStream_t s, int guard_reg, int guard_val, float dead_rel, int r_min);
 cudaError_t configure_eig_cluster_kernel();
 int eig_cluster_min();
 void set_eig_cluster_min(int r);
 cudaError_t launch_eig(const double2* G, Dim ld, Dim r, float2* U, Dim ldu, double* lam, const int* R,
                        int r_cap, int max_sweeps, double* ledger, cudaStream_t s, int guard_reg = -1, int guard_val = 0,
-                       float tol = 1e-6f, float dead_rel = 0.f, bool report_nonconv = true, bool cluster_ok = false);
+                       float tol = 1e-6f, float dead_rel = 0.f, bool report_nonconv = true, bool rough_basis = false);
 
 }  // namespace qtn
 
