@@ -44,20 +44,30 @@ __device__ __forceinline__ void ecl_circle(int u, int k, int n, int& i, int& j) 
     else { i = (u + k) % m; j = (u - k + m) % m; }
 }
 
-// Orthogonalises the W columns wx, wy (rows lane, lane + 32, ...) with one plane rotation when their inner
-// product exceeds tol of their norms, applying the same rotation to the V columns vx, vy when ACCV.  The sums
-// are butterfly reductions, so every lane holds the same bits and takes the same branch.
-template <bool ACCV>
-__device__ __forceinline__ void ecl_pair(float2* __restrict__ wx, float2* __restrict__ wy, float2* __restrict__ vx,
-                                         float2* __restrict__ vy, int r, int lane, float tol, int& rotated,
-                                         int& sig_rotated, unsigned long long& n_pairs, unsigned long long& n_rot) {
+constexpr int ECL_RPL = ECL_LD / 32;             // rows of a column held by one lane (rows lane + 32 k)
+
+// Rows of one column, in registers (rows beyond the live order are zero in shared memory).
+__device__ __forceinline__ void ecl_load(const float2* __restrict__ col, float2 (&x)[ECL_RPL], int lane) {
+#pragma unroll
+    for (int k = 0; k < ECL_RPL; ++k) x[k] = col[lane + 32 * k];
+}
+__device__ __forceinline__ void ecl_store(float2* __restrict__ col, const float2 (&x)[ECL_RPL], int lane) {
+#pragma unroll
+    for (int k = 0; k < ECL_RPL; ++k) col[lane + 32 * k] = x[k];
+}
+
+// The plane rotation that orthogonalises columns x and y (one warp, rows in registers) when their inner product
+// exceeds tol of their norms: returns false when the pair is left alone.  The sums are butterfly reductions,
+// so every lane holds the same bits and takes the same branch.
+__device__ __forceinline__ bool ecl_rotation(const float2 (&x)[ECL_RPL], const float2 (&y)[ECL_RPL], float tol,
+                                             float& cs, float& pr, float& pi, bool& sig) {
     float a = 0.f, b = 0.f, cr = 0.f, ci = 0.f;
-    for (int row = lane; row < r; row += 32) {
-        const float2 x = wx[row], y = wy[row];
-        a = fmaf(x.x, x.x, fmaf(x.y, x.y, a));
-        b = fmaf(y.x, y.x, fmaf(y.y, y.y, b));
-        cr = fmaf(x.x, y.x, fmaf(x.y, y.y, cr));      // conj(x) * y
-        ci = fmaf(x.x, y.y, fmaf(-x.y, y.x, ci));
+#pragma unroll
+    for (int k = 0; k < ECL_RPL; ++k) {
+        a = fmaf(x[k].x, x[k].x, fmaf(x[k].y, x[k].y, a));
+        b = fmaf(y[k].x, y[k].x, fmaf(y[k].y, y[k].y, b));
+        cr = fmaf(x[k].x, y[k].x, fmaf(x[k].y, y[k].y, cr));      // conj(x) * y
+        ci = fmaf(x[k].x, y[k].y, fmaf(-x[k].y, y[k].x, ci));
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -66,32 +76,56 @@ __device__ __forceinline__ void ecl_pair(float2* __restrict__ wx, float2* __rest
         cr += __shfl_xor_sync(0xffffffffu, cr, off);
         ci += __shfl_xor_sync(0xffffffffu, ci, off);
     }
-    ++n_pairs;
     const float c2 = fmaf(cr, cr, ci * ci);
     const float ab2 = a * b;
-    if (!(c2 > tol * tol * ab2) || !(c2 > 0.f) || !(ab2 > ECL_NOISE * ECL_NOISE)) return;
+    if (!(c2 > tol * tol * ab2) || !(c2 > 0.f) || !(ab2 > ECL_NOISE * ECL_NOISE)) return false;
     // Hermitian 2 x 2 problem [[a, c], [conj c, b]]: tan(theta) from zeta = (b - a) / (2 |c|), smaller root
-    const float ic = rsqrtf(c2), cabs = c2 * ic;
+    const float ic = rsqrtf(c2);
     const float zeta = 0.5f * (b - a) * ic;
     const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
-    const float cs = rsqrtf(fmaf(tt, tt, 1.f));
+    cs = rsqrtf(fmaf(tt, tt, 1.f));
     const float tc = tt * cs * ic;
-    const float pr = tc * cr, pi = tc * ci;          // p = sin(theta) c / |c|
-    (void)cabs;
-    // x' = cs x - conj(p) y ;  y' = p x + cs y   (on W and on V)
-    for (int row = lane; row < r; row += 32) {
-        const float2 x = wx[row], y = wy[row];
-        wx[row] = make_float2(fmaf(cs, x.x, -fmaf(pr, y.x, pi * y.y)), fmaf(cs, x.y, -fmaf(pr, y.y, -pi * y.x)));
-        wy[row] = make_float2(fmaf(cs, y.x, fmaf(pr, x.x, -pi * x.y)), fmaf(cs, y.y, fmaf(pr, x.y, pi * x.x)));
-        if (ACCV) {
-            const float2 u = vx[row], v = vy[row];
-            vx[row] = make_float2(fmaf(cs, u.x, -fmaf(pr, v.x, pi * v.y)), fmaf(cs, u.y, -fmaf(pr, v.y, -pi * v.x)));
-            vy[row] = make_float2(fmaf(cs, v.x, fmaf(pr, u.x, -pi * u.y)), fmaf(cs, v.y, fmaf(pr, u.y, pi * u.x)));
-        }
+    pr = tc * cr;                                   // p = sin(theta) c / |c|
+    pi = tc * ci;
+    sig = ab2 > ECL_SIG * ECL_SIG;
+    return true;
+}
+
+// x' = cs x - conj(p) y ;  y' = p x + cs y
+__device__ __forceinline__ void ecl_apply(float2 (&x)[ECL_RPL], float2 (&y)[ECL_RPL], float cs, float pr, float pi) {
+#pragma unroll
+    for (int k = 0; k < ECL_RPL; ++k) {
+        const float2 u = x[k], v = y[k];
+        x[k] = make_float2(fmaf(cs, u.x, -fmaf(pr, v.x, pi * v.y)), fmaf(cs, u.y, -fmaf(pr, v.y, -pi * v.x)));
+        y[k] = make_float2(fmaf(cs, v.x, fmaf(pr, u.x, -pi * u.y)), fmaf(cs, v.y, fmaf(pr, u.y, pi * u.x)));
+    }
+}
+
+// One pair of columns held in shared memory (W, and V when ACCV), handled by one warp.
+template <bool ACCV>
+__device__ __forceinline__ void ecl_pair(float2* __restrict__ wx, float2* __restrict__ wy, float2* __restrict__ vx,
+                                         float2* __restrict__ vy, int lane, float tol, int& rotated, int& sig_rotated,
+                                         unsigned long long& n_pairs, unsigned long long& n_rot) {
+    float2 x[ECL_RPL], y[ECL_RPL];
+    ecl_load(wx, x, lane);
+    ecl_load(wy, y, lane);
+    ++n_pairs;
+    float cs, pr, pi;
+    bool sig;
+    if (!ecl_rotation(x, y, tol, cs, pr, pi, sig)) return;
+    ecl_apply(x, y, cs, pr, pi);
+    ecl_store(wx, x, lane);
+    ecl_store(wy, y, lane);
+    if (ACCV) {
+        ecl_load(vx, x, lane);
+        ecl_load(vy, y, lane);
+        ecl_apply(x, y, cs, pr, pi);
+        ecl_store(vx, x, lane);
+        ecl_store(vy, y, lane);
     }
     ++n_rot;
     rotated = 1;
-    if (ab2 > ECL_SIG * ECL_SIG) sig_rotated = 1;
+    if (sig) sig_rotated = 1;
 }
 
 // Copies the BS live columns (W, and V when ACCV) and the column indices of `src` into buffer `dst_buf` of CTA
@@ -186,17 +220,45 @@ k_eig_cluster(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restri
                         int i, j;
                         ecl_circle(u, warp % half, BSe, i, j);
                         if (i < BS && j < BS && Z.id[i] >= 0 && Z.id[j] >= 0)
-                            ecl_pair<ACCV>(Z.W[i], Z.W[j], Z.V[i], Z.V[j], r, lane, tol, my_rot, my_sig, n_pairs,
-                                           n_rot);
+                            ecl_pair<ACCV>(Z.W[i], Z.W[j], Z.V[i], Z.V[j], lane, tol, my_rot, my_sig, n_pairs, n_rot);
                     }
                     __syncthreads();
                 }
             }
-            for (int s = 0; s < BS; ++s) {   // pairs across the two blocks, slot s: (X_i, Y_(i+s) mod BS)
-                if (warp < BS) {
-                    const int i = warp, j = (warp + s) % BS;
-                    if (X.id[i] >= 0 && Y.id[j] >= 0)
-                        ecl_pair<ACCV>(X.W[i], Y.W[j], X.V[i], Y.V[j], r, lane, tol, my_rot, my_sig, n_pairs, n_rot);
+            {   // pairs across the two blocks: warp i keeps X_i in registers, slot s pairs it with Y_(i+s) mod BS
+                const bool act = (warp < BS) && X.id[warp] >= 0;
+                float2 xw[ECL_RPL], xv[ECL_RPL];
+                if (act) {
+                    ecl_load(X.W[warp], xw, lane);
+                    if (ACCV) ecl_load(X.V[warp], xv, lane);
+                }
+                for (int s = 0; s < BS; ++s) {
+                    const int j = (warp + s) % BS;
+                    if (act && Y.id[j] >= 0) {
+                        float2 yw[ECL_RPL];
+                        ecl_load(Y.W[j], yw, lane);
+                        ++n_pairs;
+                        float cs, pr, pi;
+                        bool sig;
+                        if (ecl_rotation(xw, yw, tol, cs, pr, pi, sig)) {
+                            ecl_apply(xw, yw, cs, pr, pi);
+                            ecl_store(Y.W[j], yw, lane);
+                            if (ACCV) {
+                                float2 yv[ECL_RPL];
+                                ecl_load(Y.V[j], yv, lane);
+                                ecl_apply(xv, yv, cs, pr, pi);
+                                ecl_store(Y.V[j], yv, lane);
+                            }
+                            ++n_rot;
+                            my_rot = 1;
+                            if (sig) my_sig = 1;
+                        }
+                    }
+                    __syncthreads();
+                }
+                if (act) {
+                    ecl_store(X.W[warp], xw, lane);
+                    if (ACCV) ecl_store(X.V[warp], xv, lane);
                 }
                 __syncthreads();
             }

@@ -417,7 +417,7 @@ __device__ void eig_finish(float2* __restrict__ W, int r, double gscale, float2*
     __shared__ int col_of_rank[EIG_MAX];
     __shared__ unsigned char dead[EIG_MAX];          // by rank
     __shared__ float invn[EIG_MAX];
-    __shared__ float2 Cs[EIG_QC * EIG_CB];           // projection coefficients (finished chunk x block)
+    __shared__ __align__(16) float2 Cs[EIG_QC * EIG_CB];   // projection coefficients (finished chunk x block)
     __shared__ float2 Rb[EIG_CB * EIG_CB];           // Gram of the block, overwritten by its Cholesky factor
     __shared__ unsigned char bdead[EIG_CB];
     __shared__ int nlive_s, npre_s;
@@ -448,58 +448,76 @@ __device__ void eig_finish(float2* __restrict__ W, int r, double gscale, float2*
             // projection on the finished columns (ranks < t0), EIG_QC of them at a time
             for (int qc = 0; qc < t0; qc += EIG_QC) {
                 const int nq = min(EIG_QC, t0 - qc);
-                if (warp < nq) {
-                    const float2* wq = W + col_of_rank[qc + warp] * EIG_RS;
+                // coefficients Cs[q][c] = <finished q, block column c>: warp w takes the finished columns 2w and
+                // 2w + 1 (read once per row for both), lane (c, h) the block column c and every other row
+                if (warp < (nq + 1) / 2) {
+                    const int q0 = 2 * warp, q1 = q0 + 1;
+                    const bool two = q1 < nq;
+                    const float2* f0 = W + col_of_rank[qc + q0] * EIG_RS;
+                    const float2* f1 = W + col_of_rank[qc + (two ? q1 : q0)] * EIG_RS;
                     const int c = wl & 15, h = wl >> 4;
-                    float2 acc = make_float2(0.f, 0.f);
+                    float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;   // two chains per column
                     if (c < nb) {
                         const float2* wc = W + col_of_rank[t0 + c] * EIG_RS;
-                        float2 a1 = make_float2(0.f, 0.f), a2 = a1, a3 = a1;   // four chains
                         int row = h;
-                        for (; row + 6 < r; row += 8) {
-                            const float2 x0 = wq[row], y0 = wc[row], x1 = wq[row + 2], y1 = wc[row + 2];
-                            const float2 x2 = wq[row + 4], y2 = wc[row + 4], x3 = wq[row + 6], y3 = wc[row + 6];
-                            acc.x = fmaf(x0.x, y0.x, fmaf(x0.y, y0.y, acc.x));   // conj(x) * y
-                            acc.y = fmaf(x0.x, y0.y, fmaf(-x0.y, y0.x, acc.y));
+                        for (; row + 2 < r; row += 4) {
+                            const float2 y0 = wc[row], y1 = wc[row + 2];
+                            const float2 x0 = f0[row], x1 = f0[row + 2], z0 = f1[row], z1 = f1[row + 2];
+                            a0.x = fmaf(x0.x, y0.x, fmaf(x0.y, y0.y, a0.x));   // conj(x) * y
+                            a0.y = fmaf(x0.x, y0.y, fmaf(-x0.y, y0.x, a0.y));
                             a1.x = fmaf(x1.x, y1.x, fmaf(x1.y, y1.y, a1.x));
                             a1.y = fmaf(x1.x, y1.y, fmaf(-x1.y, y1.x, a1.y));
-                            a2.x = fmaf(x2.x, y2.x, fmaf(x2.y, y2.y, a2.x));
-                            a2.y = fmaf(x2.x, y2.y, fmaf(-x2.y, y2.x, a2.y));
-                            a3.x = fmaf(x3.x, y3.x, fmaf(x3.y, y3.y, a3.x));
-                            a3.y = fmaf(x3.x, y3.y, fmaf(-x3.y, y3.x, a3.y));
+                            b0.x = fmaf(z0.x, y0.x, fmaf(z0.y, y0.y, b0.x));
+                            b0.y = fmaf(z0.x, y0.y, fmaf(-z0.y, y0.x, b0.y));
+                            b1.x = fmaf(z1.x, y1.x, fmaf(z1.y, y1.y, b1.x));
+                            b1.y = fmaf(z1.x, y1.y, fmaf(-z1.y, y1.x, b1.y));
                         }
                         for (; row < r; row += 2) {
-                            const float2 x = wq[row], y = wc[row];
-                            acc.x = fmaf(x.x, y.x, fmaf(x.y, y.y, acc.x));
-                            acc.y = fmaf(x.x, y.y, fmaf(-x.y, y.x, acc.y));
+                            const float2 y0 = wc[row], x0 = f0[row], z0 = f1[row];
+                            a0.x = fmaf(x0.x, y0.x, fmaf(x0.y, y0.y, a0.x));
+                            a0.y = fmaf(x0.x, y0.y, fmaf(-x0.y, y0.x, a0.y));
+                            b0.x = fmaf(z0.x, y0.x, fmaf(z0.y, y0.y, b0.x));
+                            b0.y = fmaf(z0.x, y0.y, fmaf(-z0.y, y0.x, b0.y));
                         }
-                        acc.x += (a1.x + a2.x) + a3.x;
-                        acc.y += (a1.y + a2.y) + a3.y;
+                        a0.x += a1.x; a0.y += a1.y;
+                        b0.x += b1.x; b0.y += b1.y;
                     }
-                    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
-                    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
-                    if (h == 0 && c < nb) Cs[warp * EIG_CB + c] = acc;
+                    a0.x += __shfl_xor_sync(0xffffffffu, a0.x, 16);
+                    a0.y += __shfl_xor_sync(0xffffffffu, a0.y, 16);
+                    b0.x += __shfl_xor_sync(0xffffffffu, b0.x, 16);
+                    b0.y += __shfl_xor_sync(0xffffffffu, b0.y, 16);
+                    if (h == 0 && c < nb) {
+                        Cs[q0 * EIG_CB + c] = a0;
+                        if (two) Cs[q1 * EIG_CB + c] = b0;
+                    }
                 }
                 __syncthreads();
-                for (int e = tid; e < r * nb; e += EIG_THREADS) {
-                    const int c = e / r, row = e % r;
-                    float2* wc = W + col_of_rank[t0 + c] * EIG_RS;
-                    float2 acc = wc[row], acc1 = make_float2(0.f, 0.f);
-                    int q = 0;
-                    for (; q + 1 < nq; q += 2) {
-                        const float2 u0 = W[col_of_rank[qc + q] * EIG_RS + row], k0 = Cs[q * EIG_CB + c];
-                        const float2 u1 = W[col_of_rank[qc + q + 1] * EIG_RS + row], k1 = Cs[(q + 1) * EIG_CB + c];
-                        acc.x -= u0.x * k0.x - u0.y * k0.y;
-                        acc.y -= u0.x * k0.y + u0.y * k0.x;
-                        acc1.x -= u1.x * k1.x - u1.y * k1.y;
-                        acc1.y -= u1.x * k1.y + u1.y * k1.x;
+                // block -= finished Cs: thread (g, row) updates block columns 4g .. 4g + 3 of one row, reading each
+                // finished entry once
+                for (int e = tid; e < r * (EIG_CB / 4); e += EIG_THREADS) {
+                    const int g = e / r, row = e - g * r;
+                    const int c0 = 4 * g;
+                    if (c0 >= nb) continue;
+                    float2 acc[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        acc[u] = (c0 + u < nb) ? W[col_of_rank[t0 + c0 + u] * EIG_RS + row] : make_float2(0.f, 0.f);
+                    for (int q = 0; q < nq; ++q) {
+                        const float2 f = W[col_of_rank[qc + q] * EIG_RS + row];
+                        const float4 k01 = *reinterpret_cast<const float4*>(&Cs[q * EIG_CB + c0]);
+                        const float4 k23 = *reinterpret_cast<const float4*>(&Cs[q * EIG_CB + c0 + 2]);
+                        acc[0].x -= f.x * k01.x - f.y * k01.y;
+                        acc[0].y -= f.x * k01.y + f.y * k01.x;
+                        acc[1].x -= f.x * k01.z - f.y * k01.w;
+                        acc[1].y -= f.x * k01.w + f.y * k01.z;
+                        acc[2].x -= f.x * k23.x - f.y * k23.y;
+                        acc[2].y -= f.x * k23.y + f.y * k23.x;
+                        acc[3].x -= f.x * k23.z - f.y * k23.w;
+                        acc[3].y -= f.x * k23.w + f.y * k23.z;
                     }
-                    if (q < nq) {
-                        const float2 u = W[col_of_rank[qc + q] * EIG_RS + row], k = Cs[q * EIG_CB + c];
-                        acc.x -= u.x * k.x - u.y * k.y;
-                        acc.y -= u.x * k.y + u.y * k.x;
-                    }
-                    wc[row] = make_float2(acc.x + acc1.x, acc.y + acc1.y);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (c0 + u < nb) W[col_of_rank[t0 + c0 + u] * EIG_RS + row] = acc[u];
                 }
                 __syncthreads();
             }
