@@ -265,7 +265,7 @@ def run_ours(args, rank, ws, local, prec):
                 e1.record(stream)
                 e1.synchronize()
                 pt.append(e0.elapsed_time(e1))
-            for cls, name in ((0, "k_gemm"), (1, "k_eig_jacobi"), (2, "k_gemm_tc")):
+            for cls, name in ((0, "k_gemm"), (1, "k_eig"), (2, "k_gemm_tc")):
                 ms, cnt, fl = eng.profile_read(cls)
                 if cnt:
                     prof[name] = (ms, cnt, fl)
@@ -542,12 +542,17 @@ def roofline_line(r, peaks, steps: int):
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     alu_peak = sm * 128 * 2 * sm_mhz * 1e6 / 1e12
     prof = r["prof"]
-    name, (ms, cnt, fl) = max(prof.items(), key=lambda kv: kv[1][0])
+    # The eigen-solve class (the Jacobi sweeps of k_eig_cluster and k_eig_jacobi and the finishing
+    # k_eig_finish) is the dominant work; the event-timed durations of the many short GEMM launches of the
+    # eager pass include the host's launch gaps and are not used to pick it.
+    name = "k_eig" if "k_eig" in prof else max(prof.items(), key=lambda kv: kv[1][0])[0]
+    ms, cnt, fl = prof[name]
     achieved = fl / (ms / 1e3) / 1e12 if ms > 0 else 0.0
     flops_step = sum(v[2] for v in prof.values()) / steps
     t_roof = flops_step / (alu_peak * 1e12)
     t_step = r["total_ms"] / steps / 1e3
-    return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+    label = "k_eig (k_eig_cluster + k_eig_finish + k_eig_jacobi)" if name == "k_eig" else name
+    return {"bound": "alu", "kernel": label, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
             "frac": achieved / alu_peak, "traffic": None,
             "peak_source": f"FP32 FMA: {sm} SMs x 128 lanes x 2 x max SM clock {sm_mhz:.0f} MHz (derived; "
                            "MEASURED_PEAKS holds no FP32 figure)",
