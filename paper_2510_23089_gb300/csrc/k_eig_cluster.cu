@@ -295,7 +295,11 @@ k_eig_cluster(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restri
             any |= flag_all[sweep & 1][p];
             anys |= sig_all[sweep & 1][p];
         }
-        converged = (any == 0);
+        // The refinement (W out) stops once a sweep rotates no pair above the rounding level of the scaled Gram
+        // (eigenvalue products below 1e-6 of the largest squared): pairs of directions that small are left to
+        // the finishing step, which orthonormalises them after the larger ones; the rough first solve stops on
+        // no rotation at all (or at its sweep cap).
+        converged = ACCV ? (any == 0) : (anys == 0);
         last_sig = anys;
         if (tid == 0) { rot_s = 0; sig_s = 0; }
         my_rot = my_sig = 0;
