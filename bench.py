@@ -383,12 +383,13 @@ def run_batched(args, local):
             "tiles": {f"n{k[0]}_chi{k[1]}": {"tile": v[0], "ms_per_step_one_item": v[1]} for k, v in tiles.items()}}
 
 
-def run_optics(args, local):
+def run_optics(args, local, ws=1):
     """Mask-gradient workload: per item, the intensity loss of one Fresnel step after a phase mask and its
     gradient with respect to the mask's site tensors (forward pass, adjoint step, overlap derivative), at
-    n = 12 (4096 x 4096), field chi = 32, mask chi = 16.  The items are independent: each has its own
-    engine and stream and is driven from its own host thread (the library calls release the interpreter
-    lock), so their chains of small kernels run concurrently on the GPU."""
+    n = 12 (4096 x 4096), field chi = 32, one mask of chi = 16 shared by the batch.  The items are
+    independent: each has its own engine and stream and is driven from its own host thread (the library
+    calls release the interpreter lock), so their chains of small kernels run concurrently on the GPU.  The
+    items' mask gradients are summed and, with the batch sharded over ranks, all-reduced (the one exchange)."""
     from concurrent.futures import ThreadPoolExecutor
 
     import numpy as np
@@ -400,37 +401,38 @@ def run_optics(args, local):
     n, chi, chi_m = 12, 32, 16
     c = LAMBDA_Z_OVER_DX2 / (1 << n)
     enc = qtn.Engine(n_sites=n, d=4, chi=64, w=32, dense=1 << (2 * n))
+    # one phase mask for the batch (its loss is summed over the items); every item works on its own copy
+    mx, my = synth.smooth_random_phase_mask_factors(n, seed=7002, strength=0.5)
+    X, Y = qtn.MPS(n, 2, 8), qtn.MPS(n, 2, 8)
+    enc.encode(torch.from_numpy(mx.astype(np.complex64)).cuda(), n, "1d", X, 8, 1e-12, stats=False)
+    enc.encode(torch.from_numpy(my.astype(np.complex64)).cuda(), n, "1d", Y, 8, 1e-12, stats=False)
+    M = qtn.MPS(n, 4, 64)
+    enc.kron_interleave(X, Y, M)
+    enc.truncate(M, chi_m, args.cutoff, stats=False)
     items = []
     for i in range(args.items):
         E = torch.from_numpy(synth.gaussian_beam_with_rectangles(n, seed=7001 + 3 * i, waist=0.1)).cuda()
         Em = qtn.MPS(n, 4, chi)
         enc.encode(E, n, "interleaved", Em, chi, args.cutoff, stats=False)
-        mx, my = synth.smooth_random_phase_mask_factors(n, seed=7002 + 3 * i, strength=0.5)
-        X, Y = qtn.MPS(n, 2, 8), qtn.MPS(n, 2, 8)
-        enc.encode(torch.from_numpy(mx.astype(np.complex64)).cuda(), n, "1d", X, 8, 1e-12, stats=False)
-        enc.encode(torch.from_numpy(my.astype(np.complex64)).cuda(), n, "1d", Y, 8, 1e-12, stats=False)
-        M = qtn.MPS(n, 4, 64)
-        enc.kron_interleave(X, Y, M)
-        enc.truncate(M, chi_m, args.cutoff, stats=False)
         It = torch.from_numpy(synth.rectangles_target(n, seed=7003 + 3 * i).astype(np.complex64)).cuda()
         Itm = qtn.MPS(n, 4, chi_m)
         enc.encode(It, n, "interleaved", Itm, chi_m, args.cutoff, stats=False)
         del E, It
         eng = qtn.Engine(n_sites=n, d=4, chi=64, w=32, dense=0, stream=torch.cuda.Stream())
         prob = optics.IntensityLossProblem(eng, n, c, chi=chi, cutoff=args.cutoff, w_cap=16)
-        items.append((eng, prob, Em, M, Itm))
+        items.append((eng, prob, Em, M.clone(), Itm))
     del enc
     torch.cuda.synchronize()
 
     def run_item(it, passes):
         eng, prob, Em, M, Itm = it
-        loss = 0.0
+        loss, H = 0.0, None
         with torch.cuda.stream(eng.stream):
             for _ in range(passes):
                 val, cache = prob.forward(Em, M, Itm)
-                prob.backward(Em, M, cache)
+                _, H = prob.backward(Em, M, cache)
                 loss += val
-        return loss
+        return loss, H
 
     pool = ThreadPoolExecutor(max_workers=len(items))
     list(pool.map(lambda it: run_item(it, args.warmup), items))
@@ -438,19 +440,25 @@ def run_optics(args, local):
     stream = torch.cuda.current_stream()
     sampler = ClockSampler(local)
     launches0 = qtn.load_library().qtn_launch_count()
+    barrier(ws)
+    torch.cuda.synchronize()
     sampler.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for it in items:                       # every item stream starts after e0
         it[0].stream.wait_event(e0)
-    losses = list(pool.map(lambda it: run_item(it, args.steps), items))
+    res = list(pool.map(lambda it: run_item(it, args.steps), items))
+    losses = [r[0] for r in res]
     for it in items:
         ev = torch.cuda.Event()
         ev.record(it[0].stream)
         stream.wait_event(ev)
+    # the items' last mask gradients summed, and over the ranks when the items are sharded (the one exchange)
+    grad = torch.stack([r[1] for r in res]).sum(dim=0)
+    optics.sum_over_ranks_(grad)
     e1.record(stream)
     e1.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), ws)
     clocks = sampler.stop()
     launches = qtn.load_library().qtn_launch_count() - launches0
     pool.shutdown()
@@ -628,17 +636,18 @@ def main():
             print(json.dumps(line), flush=True)
         return
     if args.workload == "optics":
-        r = run_optics(args, local)
+        r = run_optics(args, local, ws)
         value = args.items * args.steps * ws / (r["ms"] / 1e3)
         line = {"metric": "intensity-loss forward + mask gradient items/s", "value": value, "unit": "items/s",
                 "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp32",
                 "data": "synthetic",
                 "config": {"workload": f"{args.items} items per step: 4096x4096 interleaved field (n=12, chi=32, "
-                                       "Gaussian beam x random rectangles), smooth phase mask (chi=16), rectangle "
-                                       "target; loss |I - I_t|^2 after one Fresnel step and its gradient with "
-                                       "respect to the mask site tensors", "mask_bonds": r["mask_bonds"],
-                           "cutoff": args.cutoff, "parallelism": f"replicas x{ws}", "launch": "eager, one engine, stream and host thread per item",
+                                       "Gaussian beam x random rectangles), one smooth phase mask (chi=16) shared "
+                                       "by the batch, rectangle targets; loss |I - I_t|^2 after one Fresnel step "
+                                       "and its gradient with respect to the mask site tensors, summed over the "
+                                       "items (all-reduced over the ranks)", "mask_bonds": r["mask_bonds"],
+                           "cutoff": args.cutoff, "parallelism": f"items sharded x{ws}, mask gradient all-reduced", "launch": "eager, one engine, stream and host thread per item",
                            "l2": "states stay L2-resident (no flush)"},
                 "clocks": r["clocks"], "gpu_launches": r["launches"], "e2e": None, "roofline": None}
         if rank == 0:

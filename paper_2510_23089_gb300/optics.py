@@ -100,6 +100,36 @@ class IntensityLossProblem:
         return G, eng.overlap_grad(M, G)
 
 
+def sum_over_ranks_(t: torch.Tensor, group=None) -> torch.Tensor:
+    """Sums `t` in place over the ranks of `group` (the default process group when None) and returns it; a
+    no-op without an initialised process group of more than one rank.
+
+    The batch of the mask-learning workload shards by item (every rank holds some of the fields and
+    targets, all ranks the same mask); the gradient of the batch loss with respect to the shared mask is
+    the sum of the per-item gradients, so this all-reduce (one mask gradient, ~100 KB at chi = 16) is the
+    only exchange between ranks.  Complex tensors are reduced through their real view."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size(group) <= 1:
+        return t
+    dist.all_reduce(torch.view_as_real(t) if t.is_complex() else t, op=dist.ReduceOp.SUM, group=group)
+    return t
+
+
+def batch_loss_and_gradient(problem: "IntensityLossProblem", fields, targets, M: "qtn.MPS", group=None):
+    """Loss summed over this rank's items (fields[i], targets[i]) for the shared mask M, and its gradient
+    with respect to M's site tensors (M's padded layout), both summed over the ranks of `group`."""
+    total, H_sum = 0.0, None
+    for E, It in zip(fields, targets):
+        loss, cache = problem.forward(E, M, It)
+        _, H = problem.backward(E, M, cache)
+        total += loss
+        H_sum = H.clone() if H_sum is None else H_sum.add_(H)
+    loss_t = torch.tensor([total], dtype=torch.float64, device=H_sum.device)
+    sum_over_ranks_(loss_t, group)
+    sum_over_ranks_(H_sum, group)
+    return float(loss_t.item()), H_sum
+
+
 class FresnelIntensityLoss(torch.autograd.Function):
     """L(mask site tensors) for a fixed field and target; backward by the adjoint above.
 

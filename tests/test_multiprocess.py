@@ -77,3 +77,51 @@ def test_reference_arm_line_has_the_contract_keys():
     assert line["unit"] == "steps/s" and line["higher_is_better"] is True and line["n_gpus"] == 1
     assert line["e2e"]["value"] == line["value"] and line["e2e"]["h2d_bytes_per_step"] == 0
     assert line["cpu_baseline"]["cores"] >= 1 and line["config"]["workload"]
+
+
+def _grad_worker(rank, port, parts, out):
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port), "RANK": str(rank),
+                       "WORLD_SIZE": "2", "LOCAL_RANK": str(rank), "CUDA_VISIBLE_DEVICES": ""})
+    sys.path.insert(0, ROOT)
+    import torch
+    import torch.distributed as dist
+    from paper_2510_23089_gb300 import optics
+    dist.init_process_group("gloo", rank=rank, world_size=2)
+    g = torch.from_numpy(parts[rank].copy())
+    optics.sum_over_ranks_(g)
+    loss = torch.tensor([float(rank + 1)], dtype=torch.float64)
+    optics.sum_over_ranks_(loss)
+    dist.destroy_process_group()
+    out.put((rank, g.numpy(), float(loss.item())))
+
+
+def test_sharded_batch_mask_gradient_is_the_sum_over_items():
+    # the mask-learning batch shards by item: four items' gradients of the intensity loss with respect to one
+    # shared mask (FP64 dense oracle, 8 x 8 fields), two per rank; the all-reduce gives every rank the sum over
+    # all four items
+    import numpy as np
+    import synth
+    from oracle import optics as OO
+    rng = np.random.default_rng(61)
+    n, c = 3, 0.4
+    M = np.exp(1j * rng.uniform(-1, 1, (8, 8)))
+    grads = []
+    for i in range(4):
+        E = synth.gaussian_beam_with_rectangles(n, seed=6100 + i, waist=0.3).astype(np.complex128)
+        It = (rng.uniform(0, 1, (8, 8)) > 0.5).astype(np.float64)
+        grads.append(OO.intensity_loss_grad_dense(E, M, It, c).astype(np.complex64))
+    parts = [grads[0] + grads[1], grads[2] + grads[3]]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = free_port()
+    procs = [ctx.Process(target=_grad_worker, args=(r, port, parts, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = sorted((q.get(timeout=120) for _ in procs), key=lambda t: t[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    total = sum(grads)
+    for rank, g, loss in got:
+        assert np.abs(g - total).max() <= 1e-6 * np.abs(total).max()
+        assert loss == 3.0
