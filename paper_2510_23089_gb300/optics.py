@@ -119,15 +119,17 @@ def batch_loss_and_gradient(problem: "IntensityLossProblem", fields, targets, M:
     """Loss summed over this rank's items (fields[i], targets[i]) for the shared mask M, and its gradient
     with respect to M's site tensors (M's padded layout), both summed over the ranks of `group`."""
     total, H_sum = 0.0, None
-    for E, It in zip(fields, targets):
-        loss, cache = problem.forward(E, M, It)
-        _, H = problem.backward(E, M, cache)
-        total += loss
-        H_sum = H.clone() if H_sum is None else H_sum.add_(H)
-    loss_t = torch.tensor([total], dtype=torch.float64, device=H_sum.device)
-    sum_over_ranks_(loss_t, group)
-    sum_over_ranks_(H_sum, group)
-    return float(loss_t.item()), H_sum
+    with torch.cuda.stream(problem.eng.stream):     # the sums follow the engine's work on its stream
+        for E, It in zip(fields, targets):
+            loss, cache = problem.forward(E, M, It)
+            _, H = problem.backward(E, M, cache)
+            total += loss
+            H_sum = H.clone() if H_sum is None else H_sum.add_(H)
+        loss_t = torch.tensor([total], dtype=torch.float64, device=H_sum.device)
+        sum_over_ranks_(loss_t, group)
+        sum_over_ranks_(H_sum, group)
+        value = float(loss_t.item())
+    return value, H_sum
 
 
 class FresnelIntensityLoss(torch.autograd.Function):
