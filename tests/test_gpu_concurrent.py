@@ -60,3 +60,24 @@ def test_threaded_items_match_sequential_run(lib):
     for (l0, h0), (l1, h1) in zip(seq, par):
         assert abs(l1 - l0) <= 1e-6 * abs(l0)
         assert np.linalg.norm(h1 - h0) <= 1e-5 * np.linalg.norm(h0)
+
+
+def test_batch_loss_and_gradient_is_the_sum_over_items(lib):
+    # one mask for a batch of fields and targets: the batch loss and its mask gradient are the sums of the
+    # items' (a single process: the all-reduce over ranks is the identity)
+    from paper_2510_23089_gb300 import optics
+    items = make_items(lib, optics, 3)
+    eng, prob, _, M, _ = items[0]
+    fields, targets = [it[2] for it in items], [it[4] for it in items]
+    loss, H = optics.batch_loss_and_gradient(prob, fields, targets, M)
+    ref_loss, ref_H = 0.0, None
+    with torch.cuda.stream(eng.stream):
+        for E, It in zip(fields, targets):
+            val, cache = prob.forward(E, M, It)
+            _, h = prob.backward(E, M, cache)
+            ref_loss += val
+            ref_H = h.clone() if ref_H is None else ref_H + h
+    eng.stream.synchronize()
+    H, ref_H = H.cpu().numpy(), ref_H.cpu().numpy()
+    assert abs(loss - ref_loss) <= 1e-6 * abs(ref_loss)
+    assert np.linalg.norm(H - ref_H) <= 1e-5 * np.linalg.norm(ref_H)
