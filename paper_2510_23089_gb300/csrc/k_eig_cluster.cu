@@ -314,44 +314,44 @@ k_eig_cluster(const double2* __restrict__ G, Dim ldd, Dim rdim, float2* __restri
             }
         }
     } else {
-    // eigenvalues: column norms of W (FP64 sums) in the units of G, published to every CTA
-    for (int h = 0; h < 2; ++h) {
-        EclBlock& B = buf[2 * par + h];
-        for (int k = warp; k < BS; k += ECL_THREADS / 32) {
-            const int j = B.id[k];
-            if (j < 0) continue;
-            double s2 = 0.0;
-            for (int row = lane; row < r; row += 32) {
-                const float2 x = B.W[k][row];
-                s2 += (double)x.x * x.x + (double)x.y * x.y;
-            }
+        // eigenvalues: column norms of W (FP64 sums) in the units of G, published to every CTA
+        for (int h = 0; h < 2; ++h) {
+            EclBlock& B = buf[2 * par + h];
+            for (int k = warp; k < BS; k += ECL_THREADS / 32) {
+                const int j = B.id[k];
+                if (j < 0) continue;
+                double s2 = 0.0;
+                for (int row = lane; row < r; row += 32) {
+                    const float2 x = B.W[k][row];
+                    s2 += (double)x.x * x.x + (double)x.y * x.y;
+                }
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
-            if (lane < ECL_C) {
-                double* la = cluster.map_shared_rank(&lam_all[0], lane);
-                la[j] = sqrt(s2) * gscale_s;
+                for (int off = 16; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+                if (lane < ECL_C) {
+                    double* la = cluster.map_shared_rank(&lam_all[0], lane);
+                    la[j] = sqrt(s2) * gscale_s;
+                }
             }
         }
-    }
-    cluster.sync();
-    // descending-eigenvalue rank of every column (ties by index); U column rank = V column, lam[rank]
-    for (int h = 0; h < 2; ++h) {
-        EclBlock& B = buf[2 * par + h];
-        for (int k = warp; k < BS; k += ECL_THREADS / 32) {
-            const int j = B.id[k];
-            if (j < 0) continue;
-            const double v = lam_all[j];
-            int rk = 0;
-            for (int i = lane; i < r; i += 32) {
-                const double u = lam_all[i];
-                rk += (u > v) || (u == v && i < j);
-            }
+        cluster.sync();
+        // descending-eigenvalue rank of every column (ties by index); U column rank = V column, lam[rank]
+        for (int h = 0; h < 2; ++h) {
+            EclBlock& B = buf[2 * par + h];
+            for (int k = warp; k < BS; k += ECL_THREADS / 32) {
+                const int j = B.id[k];
+                if (j < 0) continue;
+                const double v = lam_all[j];
+                int rk = 0;
+                for (int i = lane; i < r; i += 32) {
+                    const double u = lam_all[i];
+                    rk += (u > v) || (u == v && i < j);
+                }
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) rk += __shfl_xor_sync(0xffffffffu, rk, off);
-            for (int row = lane; row < r; row += 32) U[(long long)rk * ldu + row] = B.V[k][row];
-            if (lane == 0) lam[rk] = v;
+                for (int off = 16; off > 0; off >>= 1) rk += __shfl_xor_sync(0xffffffffu, rk, off);
+                for (int row = lane; row < r; row += 32) U[(long long)rk * ldu + row] = B.V[k][row];
+                if (lane == 0) lam[rk] = v;
+            }
         }
-    }
     }
     if (prof != nullptr && lane == 0 && (n_pairs | n_rot))
         atomicAdd(prof, 8.0 * r * (double)n_pairs + (ACCV ? 48.0 : 24.0) * r * (double)n_rot);
