@@ -81,3 +81,13 @@ def test_bench_rejects_an_unknown_precision():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--prec", "fp8"], capture_output=True,
                        text=True, timeout=300)
     assert r.returncode == 2 and "invalid choice" in r.stderr
+
+
+def test_eig_cluster_threshold_is_a_host_setting():
+    # the process-wide order threshold of the cluster eigen-solver is host state: settable without a GPU
+    import ctypes
+    from paper_2510_23089_gb300 import qtn
+    lib = qtn.load_library()
+    for r_min in (2, 32, 161, -5):
+        assert lib.qtn_set_eig_cluster_min(ctypes.c_int(r_min)) == 0
+    assert lib.qtn_set_eig_cluster_min(ctypes.c_int(32)) == 0
