@@ -82,6 +82,28 @@ def test_fresnel_step_1024(lib):
     print(f"n=10 step vs exact dense: gpu {rel(got, exact):.3e}, oracle {rel(ref, exact):.3e}")
 
 
+def test_encode_4096_matches_oracle(lib):
+    # the 4096 x 4096 field of the mask-learning workload (n = 12 interleaved sites, chi = 32, cutoff 1e-10):
+    # the first unfoldings are 4 x 4^11 and 16 x 4^10 (long, HBM-streamed Gram products)
+    n, chi, cut = 12, 32, 1e-10
+    E = synth.gaussian_beam_with_rectangles(n, seed=7001, waist=0.1)
+    E64 = E.astype(np.complex128)
+    n2 = float(np.linalg.norm(E64) ** 2)
+    # room for the read-out: every intermediate 4^p x bond[p] of the dense contraction fits the buffers
+    eng = lib.Engine(n_sites=n, d=4, chi=64, w=32, dense=1 << (2 * n + 2))
+    psi = lib.MPS(n, 4, chi)
+    st = eng.encode(torch.from_numpy(E).cuda(), n, "interleaved", psi, chi, cut)
+    got = eng.to_dense(psi, "interleaved", n).cpu().numpy()
+    sites, eps = OS.tt_svd(OQ.dense_to_quantics(E64, "interleaved"), n, 4, chi, cut)
+    ref = OQ.quantics_to_dense(OS.to_vector(sites), n, "interleaved")
+    err = rel(got, ref)
+    print(f"4096^2 encode: rel {err:.3e} eps_gpu {st.discarded / n2:.2e} eps_orc {sum(eps) / n2:.2e} "
+          f"bonds {psi.bonds()} vs {OS.bonds(sites)}")
+    assert max(abs(a - b) for a, b in zip(psi.bonds(), OS.bonds(sites))) <= 1
+    assert err <= 1e-5 + np.sqrt(st.discarded / n2) + np.sqrt(sum(eps) / n2)
+    assert abs(st.discarded - sum(eps)) <= 1e-6 * n2
+
+
 @pytest.fixture(scope="module")
 def n16(lib):
     n, chi, cut = 16, 128, 1e-10
