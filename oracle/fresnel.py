@@ -86,17 +86,30 @@ def step_passes(layout: str, n: int, Q, Qd, D):
     return passes
 
 
-def apply_sequence(passes, sites, canon: str, chi_max: int, cutoff: float, totals=None):
+def operator_canonical(W, side: str):
+    """An MPO (cores (a, s', s, b)) in left- or right-canonical form, as an MPS of the (s', s) pairs
+    (the same operator; exact QR sweeps)."""
+    as_mps = [w.reshape(w.shape[0], w.shape[1] * w.shape[2], w.shape[3]) for w in W]
+    m = _mps.left_canonicalize(as_mps) if side == "left" else _mps.right_canonicalize(as_mps)
+    return [x.reshape(x.shape[0], W[p].shape[1], W[p].shape[2], x.shape[2]) for p, x in enumerate(m)]
+
+
+def apply_sequence(passes, sites, canon: str, chi_max: int, cutoff: float, totals=None, passes_left=None):
     """Apply embedded MPOs in order by zip-up with alternating directions.
     Returns (sites, canon, total discarded weight); `totals` (a list) collects
-    the squared norms of the factorised matrices."""
+    the squared norms of the factorised matrices.  With `passes_left` (the same
+    operators in left-canonical form), a right-to-left pass applies the
+    left-canonical form and a left-to-right pass the right-canonical one
+    (`passes`), so that every operator is canonical in the direction of its sweep."""
     A = sites
     if canon == "none":
         A = _mps.left_canonicalize(A)
         canon = "left"
     disc = 0.0
-    for W in passes:
+    for i, W in enumerate(passes):
         direction = "rl" if canon == "left" else "lr"
+        if passes_left is not None and direction == "rl":
+            W = passes_left[i]
         A, eps = _apply.zipup(W, A, chi_max, cutoff, direction, totals)
         disc += sum(eps)
         canon = "right" if direction == "rl" else "left"
@@ -104,13 +117,23 @@ def apply_sequence(passes, sites, canon: str, chi_max: int, cutoff: float, total
 
 
 def fresnel_mps(sites, layout: str, n: int, c: float, chi_max: int, cutoff: float,
-                canon: str = "none", n_steps: int = 1, ops=None, totals=None):
-    """n_steps Fresnel steps on an MPS.  Returns (sites, canon, discarded)."""
+                canon: str = "none", n_steps: int = 1, ops=None, totals=None, operator_form: str = "right"):
+    """n_steps Fresnel steps on an MPS.  Returns (sites, canon, discarded).
+
+    operator_form "right": every pass applies the right-canonical operators the
+    builders deliver; "matched": each pass applies its operator in the canonical
+    form of its sweep direction (left-canonical for right-to-left passes)."""
     Q, Qd, D = ops if ops is not None else step_operators(n, c)
+    passes_left = None
+    if operator_form == "matched":
+        Q, Qd, D = (operator_canonical(op, "right") for op in (Q, Qd, D))
+        passes_left = step_passes(layout, n, *(operator_canonical(op, "left") for op in (Q, Qd, D)))
+    elif operator_form != "right":
+        raise ValueError(operator_form)
     passes = step_passes(layout, n, Q, Qd, D)
     disc = 0.0
     A = sites
     for _ in range(n_steps):
-        A, canon, d = apply_sequence(passes, A, canon, chi_max, cutoff, totals)
+        A, canon, d = apply_sequence(passes, A, canon, chi_max, cutoff, totals, passes_left)
         disc += d
     return A, canon, disc

@@ -260,6 +260,50 @@ def test_untruncated_mps_fresnel_equals_dense(layout):
     assert abs(np.linalg.norm(Ez) - np.linalg.norm(E)) < 1e-11 * np.linalg.norm(E)
 
 
+@pytest.mark.parametrize("layout", ["interleaved", "serial"])
+def test_matched_operator_form_untruncated_equals_dense(layout):
+    # operators in the canonical form of each pass's sweep direction: the same operators, so without
+    # truncation the step is still the dense propagator
+    n, c = 5, 0.3
+    E = synth.gaussian_beam_with_rectangles(n, seed=17, waist=0.2).astype(complex)
+    sites, _ = OS.tt_svd(OQ.dense_to_quantics(E, layout), OQ.n_sites(n, layout), OQ.phys_dim(layout))
+    ops = OF.step_operators(n, c, qft=OM.qft_mpo_layers(n, 1e-20), phase_cutoff=1e-20)
+    for W in ops:
+        for side in ("left", "right"):
+            Wc = OF.operator_canonical(W, side)
+            assert np.abs(OM.to_dense(Wc) - OM.to_dense(W)).max() < 1e-12
+    out, canon, disc = OF.fresnel_mps(sites, layout, n, c, 1 << 20, 0.0, canon="left", ops=ops,
+                                      operator_form="matched")
+    assert rel(OQ.quantics_to_dense(OS.to_vector(out), n, layout), OF.fresnel_dense(E, c)) < 1e-11
+
+
+def test_matched_operator_form_depends_on_the_operator_only():
+    # the matched form re-canonicalises the operators, so any representation of the same operator (here a
+    # right-canonical MPO put through random non-unitary changes of gauge) gives the same truncated step,
+    # within the truncation budget of the dense propagation
+    n, c, chi = 6, 0.45, 10
+    E = synth.gaussian_beam_with_rectangles(n, seed=19, waist=0.2).astype(complex)
+    sites, eps0 = OS.tt_svd(OQ.dense_to_quantics(E, "interleaved"), n, 4, 1 << 20, 1e-14)
+    Q = OM.qft_mpo_layers(n, 1e-14)
+    rng = np.random.default_rng(7)
+    G = [np.eye(1)] + [np.eye(Q[p].shape[3]) + 0.3 * rng.standard_normal((Q[p].shape[3],) * 2)
+                       for p in range(n - 1)] + [np.eye(1)]
+    Qg = [np.einsum("ia,atsb,bj->itsj", np.linalg.inv(G[p]), Q[p], G[p + 1]) for p in range(n)]
+    assert np.abs(OM.to_dense(Qg) - OM.to_dense(Q)).max() < 1e-12
+    D = OM.phase_mpo(n, c, 1e-14)
+    runs = []
+    for W in (Q, Qg):
+        runs.append(OF.fresnel_mps(sites, "interleaved", n, c, chi, 1e-12, canon="left",
+                                   ops=(W, OM.dagger(W), D), operator_form="matched"))
+    (a, _, da), (b, _, db) = runs
+    assert rel(OS.to_vector(b), OS.to_vector(a)) < 1e-10 and abs(da - db) < 1e-10 * OS.norm2(sites)
+    exact = OF.fresnel_dense(E, c)
+    got = OQ.quantics_to_dense(OS.to_vector(a), n, "interleaved")
+    n2 = np.linalg.norm(E) ** 2
+    assert da > 0.0
+    assert np.linalg.norm(got - exact) <= np.sqrt(2 * 6 * da) + 1e-10 * np.sqrt(n2)
+
+
 def test_fresnel_group_properties():
     n = 4
     E = synth.gaussian_beam_with_rectangles(n, seed=18, waist=0.3).astype(complex)
